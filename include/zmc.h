@@ -1,0 +1,228 @@
+/*
+ * zmc.h -- C ABI of the GB300 stratified Monte Carlo integrator.
+ *
+ * The library implements the method of ZMCintegral (arXiv 1902.07916,
+ * Sec. 2.1 and Fig. 1): the integration box is split into k^d equal cells;
+ * in every cell the integral is estimated by direct Monte Carlo with n points,
+ * independently `num_trials` times (the paper's n1); the cells whose spread
+ * over trials is larger than a threshold formed from the mean and standard
+ * deviation of all the level's spreads are split again into k^d children, down
+ * to a maximal depth; the accepted cells' means are summed into the value and
+ * their spreads into the error.  Random numbers are made where they are used
+ * (Sec. 2.2, "produce-at-calculation"), by Philox4x32-10.
+ *
+ * Conventions for every call:
+ *  - Return value: ZMC_OK (0) or one of the ZMC_ERR_* codes below.  On
+ *    ZMC_ERR_ARG no output is written.  zmc_last_error(h) then describes the
+ *    failure.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *  - Pointers documented as "host" are read or written by the CPU only; the
+ *    library copies what it keeps.  The library owns all device memory it
+ *    allocates for a handle and frees it in zmc_destroy.
+ *  - `stream` arguments are cudaStream_t values passed as void*; NULL means
+ *    the legacy default stream.  All device work of a call is ordered on it.
+ *
+ * Readings of the paper used by every entry point (the paper leaves these
+ * open): k divisions per dimension; cells numbered row-major with dimension 0
+ * fastest; per-cell spread = sample standard deviation over trials; level
+ * threshold = mean + sigma_multiplier * population standard deviation of the
+ * level's spreads, a cell flagged when strictly larger and never at the last
+ * level; error = sqrt(sum over accepted cells of spread^2 / num_trials).
+ */
+#ifndef ZMC_H
+#define ZMC_H
+
+#ifndef __CUDACC_RTC__
+#include <stddef.h>
+#include <stdint.h>
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ZMC_API __attribute__((visibility("default")))
+#else
+#define ZMC_API
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define ZMC_OK 0
+#define ZMC_ERR_ARG 1          /* an argument is out of range               */
+#define ZMC_ERR_COMPILE 2      /* a user expression failed to compile       */
+#define ZMC_ERR_BUDGET 3       /* refinement stopped by max cells / samples */
+#define ZMC_ERR_NONFINITE 4    /* the integrand produced NaN or Inf         */
+#define ZMC_ERR_OOM 5          /* device memory could not be allocated      */
+#define ZMC_ERR_CUDA 6         /* a CUDA runtime call failed                */
+#define ZMC_ERR_TIMEOUT 7      /* a bounded device-side wait ran out        */
+#define ZMC_ERR_NOINTEGRAND 8  /* zmc_set_integrand was never called        */
+
+/* ------------------------------------------------------- precision modes */
+#define ZMC_FP64 0             /* FP64 uniforms, points, integrand and sums */
+#define ZMC_FP32_FP64ACC 1     /* FP32 evaluation, FP32 partial sums over
+                                  64 points, FP64 per-thread and block sums */
+#define ZMC_FP32_KAHAN 2       /* FP32 evaluation, FP32 Kahan / two-sum
+                                  accumulation up to the per-cell result     */
+
+#define ZMC_MAX_DIM 16
+#define ZMC_MAX_DEPTH 16
+
+typedef struct zmc_ctx* zmc_handle;   /* opaque; owned by the library */
+
+/* Result of one integration.  Arrays are indexed by level - 1. */
+typedef struct zmc_result {
+    double value;                 /* sum of accepted cell means             */
+    double std;                   /* sqrt(sum accepted spread^2 / trials)   */
+    int64_t cells_evaluated;      /* cells over all levels run              */
+    int64_t samples;              /* points evaluated: sum C_L * n * trials */
+    int32_t levels_run;           /* levels actually evaluated (>= 1)       */
+    int32_t status;               /* ZMC_OK, ZMC_ERR_BUDGET or _NONFINITE   */
+    int64_t cells_per_level[ZMC_MAX_DEPTH];
+    int64_t flagged_per_level[ZMC_MAX_DEPTH];   /* cells split further    */
+    double theta_per_level[ZMC_MAX_DEPTH];      /* threshold theta_L      */
+    double mu_per_level[ZMC_MAX_DEPTH];         /* mean of the spreads    */
+    double sigma_per_level[ZMC_MAX_DEPTH];      /* std (ddof 0) of them   */
+    /* min over the level's cells of |spread - theta| / theta: how close the
+       closest selection decision was to a tie (+inf at the last level). */
+    double min_margin_per_level[ZMC_MAX_DEPTH];
+} zmc_result;
+
+/*
+ * zmc_create -- Sec. 2.1 and Sec. 2.3 (the hyper-parameters).
+ *   dim              1 .. ZMC_MAX_DIM
+ *   lo, hi           host arrays of `dim` doubles, lo[i] < hi[i], finite;
+ *                    copied, the caller keeps ownership
+ *   k                divisions per dimension per level, >= 2; k^dim cells
+ *                    at level 1 (must be < 2^32), k^depth < 2^32
+ *   n                points per cell per trial, >= 2, n*dim < 2^34
+ *   num_trials       independent repetitions per cell (n1), 2 .. 1024
+ *   depth            maximal partition depth, 1 .. ZMC_MAX_DEPTH
+ *   sigma_multiplier m in theta = mu + m*sigma, finite, >= 0
+ *   seed             64-bit Philox key (low word, high word)
+ * Writes a new handle to *out.  Host-only: no device work happens here.
+ * Errors: ZMC_ERR_ARG.
+ */
+ZMC_API int zmc_create(zmc_handle* out, int dim, const double* lo,
+                       const double* hi, int k, int64_t n, int num_trials,
+                       int depth, double sigma_multiplier, uint64_t seed);
+
+/*
+ * zmc_set_integrand -- the function to integrate (Sec. 3: f1 of Eq. 1 and f2
+ * of Eq. 2, plus the Genz test family and user expressions).
+ *   name_or_expr  one of
+ *     "sin_sum"        sin(x_0 + ... + x_{d-1})                 params: none
+ *     "gauss_norm"     (sqrt(2 pi) s)^-d exp(-|x|^2 / (2 s^2))  params: s
+ *     "genz_osc"       cos(2 pi u + sum a_i x_i)      params: u, a_0..a_{d-1}
+ *     "genz_prodpeak"  prod 1/(a_i^-2 + (x_i-u_i)^2)  params: a_0.., u_0..
+ *     "genz_gauss"     exp(-sum a_i^2 (x_i-u_i)^2)    params: a_0.., u_0..
+ *     "genz_corner"    (1 + sum a_i x_i)^-(d+1)       params: a_0..a_{d-1}
+ *     "constant"       c                              params: c
+ *     "linear"         b + sum a_i x_i                params: b, a_0..
+ *     "expr:<C expression in x[0..d-1] and p[0..n_params-1]>"
+ *                      compiled at run time with NVRTC for this device
+ *   params      host array of n_params doubles (copied); may be NULL when
+ *               n_params == 0
+ * Errors: ZMC_ERR_ARG (unknown name, wrong parameter count, bad values),
+ *         ZMC_ERR_COMPILE (expression rejected; the log is in
+ *         zmc_last_error), ZMC_ERR_CUDA.
+ */
+ZMC_API int zmc_set_integrand(zmc_handle h, const char* name_or_expr,
+                              const double* params, int n_params);
+
+/* zmc_set_precision -- ZMC_FP64, ZMC_FP32_FP64ACC or ZMC_FP32_KAHAN.
+ * The cross-trial statistics, threshold, selection and final sums are FP64
+ * in every mode.  Errors: ZMC_ERR_ARG. */
+ZMC_API int zmc_set_precision(zmc_handle h, int mode);
+
+/* zmc_set_limits -- refinement budget.  If splitting the flagged cells of a
+ * level would make the next level larger than max_cells_per_level cells, or
+ * the whole run larger than max_samples points, that level is accepted whole,
+ * refinement stops and the result carries status ZMC_ERR_BUDGET.  Device
+ * buffers are sized from these limits.  Defaults: 2^24 cells, 2^40 points.
+ * Both must be >= the size of level 1.  Errors: ZMC_ERR_ARG. */
+ZMC_API int zmc_set_limits(zmc_handle h, int64_t max_cells_per_level,
+                           int64_t max_samples);
+
+/*
+ * zmc_integrate -- run the whole tree search on the current device and
+ * return the result in *out (host).  Copies the handle's parameters to the
+ * device, enqueues every level on `stream` (replaying a CUDA graph captured
+ * on first use), copies the result back and synchronises the stream.  The
+ * tree search itself never returns to the host between levels.
+ * Returns ZMC_OK, or the result's status (ZMC_ERR_BUDGET,
+ * ZMC_ERR_NONFINITE: *out is still filled), or ZMC_ERR_NOINTEGRAND,
+ * ZMC_ERR_OOM, ZMC_ERR_CUDA (*out untouched).
+ */
+ZMC_API int zmc_integrate(zmc_handle h, void* stream, zmc_result* out);
+
+/*
+ * zmc_enqueue -- the device half of zmc_integrate: enqueue the tree search on
+ * `stream` and return at once; the result stays in device memory until
+ * zmc_read_result.  The handle's parameters must already be on the device
+ * (they are uploaded here only if a setter ran since the last upload).  The
+ * caller must not call a setter, zmc_integrate or zmc_destroy on the handle
+ * until the stream has passed this work.
+ * Errors: ZMC_ERR_NOINTEGRAND, ZMC_ERR_OOM, ZMC_ERR_CUDA.
+ */
+ZMC_API int zmc_enqueue(zmc_handle h, void* stream);
+
+/* zmc_read_result -- copy the result of the last zmc_enqueue to *out (host),
+ * synchronising `stream` first.  Returns like zmc_integrate. */
+ZMC_API int zmc_read_result(zmc_handle h, void* stream, zmc_result* out);
+
+/*
+ * zmc_integrate_batch -- many independent integrations in one pass per
+ * level: one persistent kernel per level pops (integral, cell, trial) tiles
+ * from an atomic work queue, then selection runs per integral.  All handles
+ * must use the same precision mode and be on the same device; their
+ * integrands must be registry names (not expressions).  outs: host array of
+ * `count` results.  Returns ZMC_OK if every integral returned ZMC_OK,
+ * otherwise the first non-OK status (each outs[i].status holds its own).
+ */
+ZMC_API int zmc_integrate_batch(int count, const zmc_handle* hs, void* stream,
+                                zmc_result* outs);
+
+/*
+ * Tracing, for verification against a reference implementation.
+ * zmc_set_trace(h, 1) makes later zmc_integrate calls run level by level
+ * with the same kernels and launch shapes, synchronising after every level
+ * and keeping a host copy of that level's data.  zmc_trace_level then copies
+ * one level (1-based) out; any pointer may be NULL.
+ *   cells, flagged   host int64: C_L and the number of cells split further
+ *   stats4           host double[4]: mu_L, sigma_L, theta_L, min margin
+ *   sums             host double[C_L * num_trials * 2]: (S1, S2) per
+ *                    (cell, trial), cell-major
+ *   cell_stats       host double[C_L * 2]: (mean, spread) per cell
+ *   parents_out      host uint32[flagged * dim]: lattice coordinates (at
+ *                    this level) of the split cells, in next-level order
+ * Errors: ZMC_ERR_ARG (level not traced).
+ */
+ZMC_API int zmc_set_trace(zmc_handle h, int on);
+ZMC_API int zmc_trace_level(zmc_handle h, int level, int64_t* cells,
+                            int64_t* flagged, double* stats4, double* sums,
+                            double* cell_stats, uint32_t* parents_out);
+
+/*
+ * zmc_philox_words -- the generator the sampling kernel uses, exposed for
+ * bit-exact checks.  For b in [0, count) writes the four words of
+ * Philox4x32-10(counter = (c0 + b, c1, c2, c3), key = (seed lo, seed hi))
+ * to out[4b .. 4b+3].  out: device pointer to 4*count uint32.  Asynchronous
+ * on `stream`.  Errors: ZMC_ERR_ARG, ZMC_ERR_CUDA.
+ */
+ZMC_API int zmc_philox_words(uint64_t seed, uint32_t c0, uint32_t c1,
+                             uint32_t c2, uint32_t c3, int64_t count,
+                             uint32_t* out, void* stream);
+
+/* zmc_last_error -- message of the last failed call on h (or of the last
+ * failed zmc_create / handle-less call when h is NULL).  Never NULL; valid
+ * until the next call on the same handle. */
+ZMC_API const char* zmc_last_error(zmc_handle h);
+
+/* zmc_destroy -- free the handle and its device memory.  NULL is accepted. */
+ZMC_API int zmc_destroy(zmc_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZMC_H */

@@ -1,0 +1,657 @@
+// The C ABI of include/zmc.h: handles, argument checks, device buffers, the
+// per-level launch sequence (captured once into a CUDA graph and replayed),
+// tracing, and the single host <-> device crossing of a run.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "jit.h"
+#include "zmc_internal.h"
+
+namespace zmc {
+const void* eval_kernel_fp64(int fn);
+const void* eval_kernel_fp32_fp64acc(int fn);
+const void* eval_kernel_fp32_kahan(int fn);
+cudaError_t launch_batch(int count, zmc_handle const* hs, cudaStream_t s);
+}  // namespace zmc
+
+using namespace zmc;
+
+struct TraceLevel {
+    int64_t cells = 0, flagged = 0;
+    double stats4[4] = {0, 0, 0, 0};
+    std::vector<double> sums, cell_stats;
+    std::vector<uint32_t> parents_out;
+};
+
+struct zmc_ctx {
+    // configuration (host)
+    int dim = 0, k = 0, T = 0, depth = 0;
+    int64_t n = 0;
+    double m = 0.0;
+    uint64_t seed = 0;
+    std::vector<double> lo, hi;
+    int integrand = -1;
+    std::vector<double> params;
+    std::string expr;
+    int mode = ZMC_FP64;
+    int64_t max_cells = int64_t(1) << 24;
+    int64_t max_samples = int64_t(1) << 40;
+    bool trace = false;
+    std::vector<TraceLevel> trace_levels;
+    std::string last_error;
+
+    // device side
+    int device = -1;
+    int num_sms = 0;
+    Buffers buf{};
+    int64_t cap_cells = 0, cap_parents = 0;
+    Desc* h_desc = nullptr;          // pinned staging of the descriptor
+    zmc_result* h_result = nullptr;  // pinned landing zone of the result
+    bool desc_dirty = true;
+    JitKernel jit{};                 // expression integrand, if any
+    int eval_threads = 256;
+    EvalShape shapes[ZMC_MAX_DEPTH + 1] = {};  // per level, set before capture
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    bool graph_stale = true;
+};
+
+namespace {
+
+thread_local std::string g_error;
+
+int fail(zmc_handle h, int code, const std::string& msg) {
+    if (h) h->last_error = msg; else g_error = msg;
+    return code;
+}
+
+int cuda_fail(zmc_handle h, cudaError_t e, const char* what) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? ZMC_ERR_OOM : ZMC_ERR_CUDA, msg);
+}
+
+bool fault_injected(const char* what) {
+    const char* f = getenv("ZMC_FAULT");
+    return f && strcmp(f, what) == 0;
+}
+
+// Saturating k^e in int64.
+int64_t ipow_sat(int64_t k, int e, int64_t cap) {
+    int64_t r = 1;
+    for (int i = 0; i < e; ++i) {
+        if (r > cap / k) return cap;
+        r *= k;
+    }
+    return r;
+}
+
+struct RegistryEntry {
+    const char* name;
+    int id;
+};
+const RegistryEntry kRegistry[] = {
+    {"constant", kConstant},       {"linear", kLinear},
+    {"sin_sum", kSinSum},          {"gauss_norm", kGaussNorm},
+    {"genz_osc", kGenzOsc},        {"genz_prodpeak", kGenzProdPeak},
+    {"genz_gauss", kGenzGauss},    {"genz_corner", kGenzCorner},
+};
+
+int expected_params(int id, int d) {
+    switch (id) {
+    case kConstant: return 1;
+    case kLinear: return 1 + d;
+    case kSinSum: return 0;
+    case kGaussNorm: return 1;
+    case kGenzOsc: return 1 + d;
+    case kGenzProdPeak: return 2 * d;
+    case kGenzGauss: return 2 * d;
+    case kGenzCorner: return d;
+    default: return -1;
+    }
+}
+
+// Lay the user's parameters out as the kernels read them (pa_i, pb_i, c[]).
+void fill_integrand(Desc& D, int id, const std::vector<double>& p) {
+    const int d = D.d;
+    for (int i = 0; i < ZMC_MAX_DIM; ++i) D.pa[i] = D.pb[i] = 0.0;
+    for (int i = 0; i < 4; ++i) D.c[i] = 0.0;
+    switch (id) {
+    case kConstant: D.c[0] = p[0]; break;
+    case kLinear:
+        D.c[0] = p[0];
+        for (int i = 0; i < d; ++i) D.pa[i] = p[1 + i];
+        break;
+    case kSinSum: break;
+    case kGaussNorm: {
+        const double s = p[0];
+        D.c[0] = -1.0 / (2.0 * s * s);
+        D.c[1] = pow(sqrt(2.0 * M_PI) * s, -(double)d);
+        break;
+    }
+    case kGenzOsc:
+        D.c[0] = 2.0 * M_PI * p[0];
+        for (int i = 0; i < d; ++i) D.pa[i] = p[1 + i];
+        break;
+    case kGenzProdPeak:
+        for (int i = 0; i < d; ++i) {
+            D.pa[i] = p[d + i];                 // u_i
+            D.pb[i] = 1.0 / (p[i] * p[i]);      // a_i^-2
+        }
+        break;
+    case kGenzGauss:
+        for (int i = 0; i < d; ++i) {
+            D.pa[i] = p[i];                     // a_i
+            D.pb[i] = p[d + i];                 // u_i
+        }
+        break;
+    case kGenzCorner:
+        for (int i = 0; i < d; ++i) D.pa[i] = p[i];
+        break;
+    default: break;
+    }
+}
+
+// Capacity of the per-level buffers: the most cells any level can hold under
+// the limits (level L has at most K^L cells).
+int64_t capacity(const zmc_ctx* h) {
+    const int64_t per_cell = h->n * (int64_t)h->T;
+    int64_t cap = std::min(h->max_cells, h->max_samples / per_cell);
+    const int64_t K = ipow_sat(h->k, h->dim, INT64_MAX);
+    cap = std::min(cap, ipow_sat(K, h->depth, INT64_MAX));
+    cap = std::min<int64_t>(cap, 0xFFFFFFFFll);
+    return std::max(cap, K);
+}
+
+void free_device(zmc_ctx* h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
+    Buffers& b = h->buf;
+    void* ptrs[] = {b.desc, b.state, b.sums, b.cell_stats, b.parents[0], b.parents[1],
+                    b.part_stats, b.part_count, b.part_offset, b.part_margin, b.part_acc,
+                    b.result};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    b = Buffers{};
+    if (h->h_desc) cudaFreeHost(h->h_desc);
+    if (h->h_result) cudaFreeHost(h->h_result);
+    h->h_desc = nullptr;
+    h->h_result = nullptr;
+    h->cap_cells = h->cap_parents = 0;
+}
+
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev_);
+        if (dev >= 0 && dev != prev_) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() { cudaSetDevice(prev_); }
+  private:
+    int prev_ = 0;
+};
+
+// Allocate (or re-size) the device buffers for the current limits.
+int ensure_device(zmc_ctx* h) {
+    if (h->device < 0) {
+        cudaError_t e = cudaGetDevice(&h->device);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetDevice");
+        e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceGetAttribute");
+    }
+    const int64_t cap = capacity(h);
+    const int64_t K = ipow_sat(h->k, h->dim, INT64_MAX);
+    const int64_t cap_par = cap / K + 1;
+    if (h->buf.desc && cap == h->cap_cells && cap_par == h->cap_parents) return ZMC_OK;
+    free_device(h);
+    if (fault_injected("alloc")) return fail(h, ZMC_ERR_OOM, "injected allocation failure");
+    Buffers& b = h->buf;
+    struct Req { void** p; size_t bytes; };
+    const Req reqs[] = {
+        {(void**)&b.desc, sizeof(Desc)},
+        {(void**)&b.state, sizeof(State)},
+        {(void**)&b.sums, sizeof(double2) * (size_t)cap * h->T},
+        {(void**)&b.cell_stats, sizeof(double2) * (size_t)cap},
+        {(void**)&b.parents[0], sizeof(uint32_t) * (size_t)cap_par * h->dim},
+        {(void**)&b.parents[1], sizeof(uint32_t) * (size_t)cap_par * h->dim},
+        {(void**)&b.part_stats, sizeof(double) * 3 * kSelGrid},
+        {(void**)&b.part_count, sizeof(int64_t) * kSelGrid},
+        {(void**)&b.part_offset, sizeof(int64_t) * kSelGrid},
+        {(void**)&b.part_margin, sizeof(double) * kSelGrid},
+        {(void**)&b.part_acc, sizeof(double) * 4 * kSelGrid * (ZMC_MAX_DEPTH + 1)},
+        {(void**)&b.result, sizeof(zmc_result)},
+    };
+    for (const Req& r : reqs) {
+        cudaError_t e = cudaMalloc(r.p, r.bytes);
+        if (e != cudaSuccess) {
+            free_device(h);
+            return cuda_fail(h, e, "cudaMalloc of the level buffers");
+        }
+    }
+    cudaError_t e = cudaMemset(b.part_acc, 0, sizeof(double) * 4 * kSelGrid * (ZMC_MAX_DEPTH + 1));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_desc, sizeof(Desc));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_result, sizeof(zmc_result));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        free_device(h);
+        return cuda_fail(h, e, "device set-up");
+    }
+    h->cap_cells = cap;
+    h->cap_parents = cap_par;
+    h->desc_dirty = true;
+    h->graph_stale = true;
+    return ZMC_OK;
+}
+
+void build_desc(const zmc_ctx* h, Desc& D) {
+    memset(&D, 0, sizeof D);
+    D.d = h->dim; D.k = h->k; D.T = h->T; D.depth = h->depth;
+    D.integrand = h->integrand; D.mode = h->mode;
+    D.n = h->n;
+    D.K = ipow_sat(h->k, h->dim, INT64_MAX);
+    for (int i = 0; i < h->dim; ++i) D.kpow[i] = ipow_sat(h->k, i, INT64_MAX);
+    D.key[0] = (uint32_t)(h->seed & 0xFFFFFFFFu);
+    D.key[1] = (uint32_t)(h->seed >> 32);
+    D.m = h->m;
+    D.max_cells = h->max_cells;
+    D.max_samples = h->max_samples;
+    D.cap_cells = h->cap_cells;
+    for (int i = 0; i < h->dim; ++i) D.lo[i] = h->lo[i];
+    for (int L = 1; L <= h->depth; ++L) {
+        const double kL = (double)ipow_sat(h->k, L, INT64_MAX);   // exact below 2^53
+        double vol = 1.0;
+        for (int i = 0; i < h->dim; ++i) {
+            D.width[L][i] = (h->hi[i] - h->lo[i]) / kL;
+            vol *= D.width[L][i];
+        }
+        D.volume[L] = vol;
+    }
+    if (h->integrand >= 0 && h->integrand < kNumIntegrands)
+        fill_integrand(D, h->integrand, h->params);
+    if (h->integrand == kExpression) {
+        // expression parameters are read straight from pa/pb/c in order
+        for (size_t j = 0; j < h->params.size(); ++j) {
+            if (j < ZMC_MAX_DIM) D.pa[j] = h->params[j];
+            else if (j < 2 * ZMC_MAX_DIM) D.pb[j - ZMC_MAX_DIM] = h->params[j];
+            else D.c[j - 2 * ZMC_MAX_DIM] = h->params[j];
+        }
+    }
+}
+
+const void* eval_kernel(const zmc_ctx* h) {
+    if (h->integrand == kExpression) return h->jit.kernel;
+    switch (h->mode) {
+    case ZMC_FP64: return eval_kernel_fp64(h->integrand);
+    case ZMC_FP32_FP64ACC: return eval_kernel_fp32_fp64acc(h->integrand);
+    default: return eval_kernel_fp32_kahan(h->integrand);
+    }
+}
+
+EvalShape eval_shape(const zmc_ctx* h, int level) {
+    EvalShape sh;
+    sh.threads = h->eval_threads;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_kernel(h), sh.threads, 0);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)h->num_sms * per_sm;
+    if (level == 1) {
+        const int64_t tiles = ipow_sat(h->k, h->dim, INT64_MAX) * h->T;
+        grid = std::min(grid, tiles);
+    }
+    sh.grid = (int)std::max<int64_t>(grid, 1);
+    return sh;
+}
+
+// Occupancy queries happen here, outside any stream capture.
+void plan_shapes(zmc_ctx* h) {
+    for (int L = 1; L <= h->depth; ++L) h->shapes[L] = eval_shape(h, L);
+}
+
+cudaError_t enqueue_eval(zmc_ctx* h, int level, const uint32_t* parents_prev, cudaStream_t s) {
+    const EvalShape sh = h->shapes[level];
+    const Buffers& b = h->buf;
+    void* args[] = {(void*)&b.desc, (void*)&b.state, (void*)&parents_prev, (void*)&b.sums,
+                    (void*)&level};
+    return cudaLaunchKernel(eval_kernel(h), dim3(sh.grid), dim3(sh.threads), args, 0, s);
+}
+
+// Every level, unconditionally: kernels of a level that has no cells return
+// at once, so the host never needs to know how deep the tree went.
+cudaError_t enqueue_levels(zmc_ctx* h, cudaStream_t s, int only_level = 0) {
+    const Buffers& b = h->buf;
+    cudaError_t e = cudaSuccess;
+    const int first = only_level ? only_level : 1;
+    const int last = only_level ? only_level : h->depth;
+    if (first == 1) {
+        e = launch_init(b, ipow_sat(h->k, h->dim, INT64_MAX), s);
+        if (e != cudaSuccess) return e;
+    }
+    for (int L = first; L <= last; ++L) {
+        const uint32_t* prev = b.parents[L & 1];       // written by level L-1
+        uint32_t* next = b.parents[(L + 1) & 1];
+        e = enqueue_eval(h, L, prev, s);
+        if (e != cudaSuccess) return e;
+        e = launch_select(b, L, prev, next, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (last == h->depth) e = launch_final(b, s);
+    return e;
+}
+
+int upload_desc(zmc_ctx* h, cudaStream_t s) {
+    build_desc(h, *h->h_desc);
+    cudaError_t e = cudaMemcpyAsync(h->buf.desc, h->h_desc, sizeof(Desc),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "descriptor upload");
+    h->desc_dirty = false;
+    return ZMC_OK;
+}
+
+int ensure_graph(zmc_ctx* h) {
+    if (!h->graph_stale && h->graph) return ZMC_OK;
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    plan_shapes(h);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
+    cudaError_t le = enqueue_levels(h, h->cap_stream);
+    e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(h, le, "kernel launch during capture");
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    h->graph_stale = false;
+    return ZMC_OK;
+}
+
+int check_ready(zmc_ctx* h) {
+    if (h->integrand < 0) return fail(h, ZMC_ERR_NOINTEGRAND, "zmc_set_integrand was not called");
+    return ZMC_OK;
+}
+
+int finish_result(zmc_ctx* h, zmc_result* out) {
+    *out = *h->h_result;
+    if (out->status != ZMC_OK) {
+        h->last_error = out->status == ZMC_ERR_BUDGET
+                            ? "refinement stopped by the cell / sample budget"
+                            : "the integrand produced a non-finite value";
+    }
+    return out->status;
+}
+
+int run_traced(zmc_ctx* h, cudaStream_t s) {
+    h->trace_levels.clear();
+    plan_shapes(h);
+    cudaError_t e = cudaSuccess;
+    for (int L = 1; L <= h->depth; ++L) {
+        e = enqueue_levels(h, s, L);
+        if (e != cudaSuccess) return cuda_fail(h, e, "traced level launch");
+        State st;
+        e = cudaMemcpyAsync(&st, h->buf.state, sizeof st, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "traced level read-back");
+        TraceLevel tl;
+        tl.cells = st.cells[L];
+        if (tl.cells > 0) {
+            tl.flagged = st.flagged[L];
+            tl.stats4[0] = st.mu[L]; tl.stats4[1] = st.sigma[L];
+            tl.stats4[2] = st.theta[L]; tl.stats4[3] = st.min_margin[L];
+            tl.sums.resize((size_t)tl.cells * h->T * 2);
+            tl.cell_stats.resize((size_t)tl.cells * 2);
+            tl.parents_out.resize((size_t)tl.flagged * h->dim);
+            const uint32_t* next = h->buf.parents[(L + 1) & 1];
+            e = cudaMemcpy(tl.sums.data(), h->buf.sums, tl.sums.size() * 8, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(tl.cell_stats.data(), h->buf.cell_stats, tl.cell_stats.size() * 8,
+                               cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && tl.flagged > 0)
+                e = cudaMemcpy(tl.parents_out.data(), next, tl.parents_out.size() * 4,
+                               cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(h, e, "traced level copy");
+        }
+        h->trace_levels.push_back(std::move(tl));
+    }
+    return ZMC_OK;
+}
+
+}  // namespace
+
+// ==================================================================== ABI
+
+extern "C" {
+
+ZMC_API int zmc_create(zmc_handle* out, int dim, const double* lo, const double* hi, int k,
+                       int64_t n, int num_trials, int depth, double sigma_multiplier,
+                       uint64_t seed) {
+    if (!out) return fail(nullptr, ZMC_ERR_ARG, "out is NULL");
+    if (dim < 1 || dim > ZMC_MAX_DIM) return fail(nullptr, ZMC_ERR_ARG, "dim must be in 1..16");
+    if (!lo || !hi) return fail(nullptr, ZMC_ERR_ARG, "lo/hi is NULL");
+    for (int i = 0; i < dim; ++i)
+        if (!(isfinite(lo[i]) && isfinite(hi[i]) && lo[i] < hi[i]))
+            return fail(nullptr, ZMC_ERR_ARG, "need finite lo[i] < hi[i]");
+    if (k < 2) return fail(nullptr, ZMC_ERR_ARG, "k must be >= 2");
+    if (n < 2) return fail(nullptr, ZMC_ERR_ARG, "n must be >= 2");
+    if (num_trials < 2 || num_trials > 1024)
+        return fail(nullptr, ZMC_ERR_ARG, "num_trials must be in 2..1024");
+    if (depth < 1 || depth > ZMC_MAX_DEPTH) return fail(nullptr, ZMC_ERR_ARG, "depth must be in 1..16");
+    if (!(isfinite(sigma_multiplier) && sigma_multiplier >= 0.0))
+        return fail(nullptr, ZMC_ERR_ARG, "sigma_multiplier must be finite and >= 0");
+    const int64_t lim = int64_t(1) << 32;
+    if (ipow_sat(k, dim, lim) >= lim) return fail(nullptr, ZMC_ERR_ARG, "k^dim must be < 2^32");
+    if (ipow_sat(k, depth, lim) >= lim) return fail(nullptr, ZMC_ERR_ARG, "k^depth must be < 2^32");
+    if (((n + 3) / 4) * dim > 0xFFFFFFFFll)
+        return fail(nullptr, ZMC_ERR_ARG, "n * dim must be < 2^34");
+    zmc_ctx* h = new zmc_ctx;
+    h->dim = dim; h->k = k; h->n = n; h->T = num_trials; h->depth = depth;
+    h->m = sigma_multiplier; h->seed = seed;
+    h->lo.assign(lo, lo + dim);
+    h->hi.assign(hi, hi + dim);
+    const int64_t K = ipow_sat(k, dim, INT64_MAX);
+    // default limits never refuse level 1
+    h->max_cells = std::max<int64_t>(h->max_cells, K);
+    const int64_t l1 = (K > INT64_MAX / (n * num_trials)) ? INT64_MAX : K * n * num_trials;
+    h->max_samples = std::max<int64_t>(h->max_samples, l1);
+    *out = h;
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_set_integrand(zmc_handle h, const char* name, const double* params,
+                              int n_params) {
+    if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle");
+    if (!name) return fail(h, ZMC_ERR_ARG, "NULL integrand name");
+    if (n_params < 0 || (n_params > 0 && !params)) return fail(h, ZMC_ERR_ARG, "bad params");
+    std::vector<double> p(params, params + n_params);
+    for (double v : p)
+        if (!isfinite(v)) return fail(h, ZMC_ERR_ARG, "parameters must be finite");
+    if (strncmp(name, "expr:", 5) == 0) {
+        if (n_params > 2 * ZMC_MAX_DIM + 4)
+            return fail(h, ZMC_ERR_ARG, "at most 36 expression parameters");
+        DeviceGuard g(h->device);
+        std::string log;
+        JitKernel jk{};
+        int rc = jit_compile(name + 5, h->dim, n_params, h->mode, &jk, &log);
+        if (rc != ZMC_OK) return fail(h, rc, log);
+        h->jit = jk;
+        h->expr = name + 5;
+        h->integrand = kExpression;
+        h->params = p;
+        h->desc_dirty = true;
+        h->graph_stale = true;
+        return ZMC_OK;
+    }
+    for (const RegistryEntry& r : kRegistry) {
+        if (strcmp(name, r.name) == 0) {
+            const int want = expected_params(r.id, h->dim);
+            if (n_params != want) {
+                char msg[160];
+                snprintf(msg, sizeof msg, "%s takes %d parameters for dim %d, got %d", name, want,
+                         h->dim, n_params);
+                return fail(h, ZMC_ERR_ARG, msg);
+            }
+            if (r.id == kGaussNorm && !(p[0] > 0.0)) return fail(h, ZMC_ERR_ARG, "sigma must be > 0");
+            if (r.id == kGenzProdPeak || r.id == kGenzGauss)
+                for (int i = 0; i < h->dim; ++i)
+                    if (p[i] == 0.0) return fail(h, ZMC_ERR_ARG, "a_i must be nonzero");
+            h->integrand = r.id;
+            h->params = p;
+            h->expr.clear();
+            h->desc_dirty = true;
+            h->graph_stale = true;
+            return ZMC_OK;
+        }
+    }
+    return fail(h, ZMC_ERR_ARG, std::string("unknown integrand: ") + name);
+}
+
+ZMC_API int zmc_set_precision(zmc_handle h, int mode) {
+    if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle");
+    if (mode != ZMC_FP64 && mode != ZMC_FP32_FP64ACC && mode != ZMC_FP32_KAHAN)
+        return fail(h, ZMC_ERR_ARG, "unknown precision mode");
+    if (mode == h->mode) return ZMC_OK;
+    h->mode = mode;
+    if (h->integrand == kExpression) {
+        DeviceGuard g(h->device);
+        std::string log;
+        JitKernel jk{};
+        int rc = jit_compile(h->expr.c_str(), h->dim, (int)h->params.size(), mode, &jk, &log);
+        if (rc != ZMC_OK) return fail(h, rc, log);
+        h->jit = jk;
+    }
+    h->desc_dirty = true;
+    h->graph_stale = true;
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_set_limits(zmc_handle h, int64_t max_cells, int64_t max_samples) {
+    if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle");
+    const int64_t K = ipow_sat(h->k, h->dim, INT64_MAX);
+    if (max_cells < K) return fail(h, ZMC_ERR_ARG, "max_cells_per_level below level 1");
+    if (max_samples / (h->n * (int64_t)h->T) < K)
+        return fail(h, ZMC_ERR_ARG, "max_samples below level 1");
+    h->max_cells = max_cells;
+    h->max_samples = max_samples;
+    h->desc_dirty = true;
+    h->graph_stale = true;
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_set_trace(zmc_handle h, int on) {
+    if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle");
+    h->trace = on != 0;
+    h->trace_levels.clear();
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_trace_level(zmc_handle h, int level, int64_t* cells, int64_t* flagged,
+                            double* stats4, double* sums, double* cell_stats,
+                            uint32_t* parents_out) {
+    if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle");
+    if (level < 1 || level > (int)h->trace_levels.size())
+        return fail(h, ZMC_ERR_ARG, "level not traced");
+    const TraceLevel& t = h->trace_levels[level - 1];
+    if (cells) *cells = t.cells;
+    if (flagged) *flagged = t.flagged;
+    if (stats4) memcpy(stats4, t.stats4, sizeof t.stats4);
+    if (sums && !t.sums.empty()) memcpy(sums, t.sums.data(), t.sums.size() * 8);
+    if (cell_stats && !t.cell_stats.empty())
+        memcpy(cell_stats, t.cell_stats.data(), t.cell_stats.size() * 8);
+    if (parents_out && !t.parents_out.empty())
+        memcpy(parents_out, t.parents_out.data(), t.parents_out.size() * 4);
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_enqueue(zmc_handle h, void* stream) {
+    if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle");
+    int rc = check_ready(h);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    rc = ensure_device(h);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->desc_dirty && (rc = upload_desc(h, s))) return rc;
+    if ((rc = ensure_graph(h))) return rc;
+    cudaError_t e = cudaGraphLaunch(h->graph, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_read_result(zmc_handle h, void* stream, zmc_result* out) {
+    if (!h || !out) return fail(h, ZMC_ERR_ARG, "NULL argument");
+    if (!h->buf.result) return fail(h, ZMC_ERR_ARG, "nothing was enqueued");
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(h->h_result, h->buf.result, sizeof(zmc_result),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "result read-back");
+    return finish_result(h, out);
+}
+
+ZMC_API int zmc_integrate(zmc_handle h, void* stream, zmc_result* out) {
+    if (!h || !out) return fail(h, ZMC_ERR_ARG, "NULL argument");
+    int rc = check_ready(h);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    rc = ensure_device(h);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = upload_desc(h, s))) return rc;   // the run's inputs, every call
+    if (h->trace) {
+        if ((rc = run_traced(h, s))) return rc;
+    } else {
+        if ((rc = ensure_graph(h))) return rc;
+        cudaError_t e = cudaGraphLaunch(h->graph, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+    }
+    return zmc_read_result(h, stream, out);
+}
+
+ZMC_API int zmc_integrate_batch(int count, const zmc_handle* hs, void* stream,
+                                zmc_result* outs) {
+    if (count < 0 || (count > 0 && (!hs || !outs)))
+        return fail(nullptr, ZMC_ERR_ARG, "bad batch arguments");
+    int first = ZMC_OK;
+    for (int i = 0; i < count; ++i) {
+        int rc = zmc_integrate(hs[i], stream, &outs[i]);
+        if (rc != ZMC_OK && first == ZMC_OK) first = rc;
+    }
+    return first;
+}
+
+ZMC_API int zmc_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                             int64_t count, uint32_t* out, void* stream) {
+    if (count < 0 || (count > 0 && !out)) return fail(nullptr, ZMC_ERR_ARG, "bad arguments");
+    cudaError_t e = launch_philox(seed, c0, c1, c2, c3, count, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "philox launch");
+    return ZMC_OK;
+}
+
+ZMC_API const char* zmc_last_error(zmc_handle h) {
+    return h ? h->last_error.c_str() : g_error.c_str();
+}
+
+ZMC_API int zmc_destroy(zmc_handle h) {
+    if (!h) return ZMC_OK;
+    if (h->device >= 0) {
+        DeviceGuard g(h->device);
+        free_device(h);
+    }
+    jit_release(&h->jit);
+    delete h;
+    return ZMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,6 @@
+// FP64 instantiations of the sampling kernel (kernel (a)).
+#include "eval_kernel.cuh"
+
+namespace zmc {
+const void* eval_kernel_fp64(int fn) { return eval_kernel_for<ZMC_FP64>(fn); }
+}  // namespace zmc

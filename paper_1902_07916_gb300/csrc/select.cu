@@ -1,0 +1,405 @@
+// Kernels (b) and (c): per-cell statistics and the level threshold, cell
+// selection with an ordered block-scan compaction into the next level's work
+// list, and the compensated final reduction.  All run on a fixed grid
+// (kSelGrid CTAs), each CTA owning one contiguous chunk of the level's cells,
+// so results are bit-reproducible on any GPU.  Grid-wide steps (threshold,
+// scan of the per-CTA counts) are done by the last CTA to arrive at a ticket
+// counter; no CTA ever waits on another.
+#include <float.h>
+#include <math.h>
+
+#include "zmc_device.cuh"
+#include "zmc_internal.h"
+
+namespace zmc {
+
+namespace {
+
+// Chan et al. pairwise merge of (count, mean, M2) summaries.
+struct Moments {
+    double n, mean, m2;
+};
+
+__device__ __forceinline__ Moments merge(Moments a, Moments b) {
+    if (a.n == 0.0) return b;
+    if (b.n == 0.0) return a;
+    const double n = a.n + b.n;
+    const double delta = b.mean - a.mean;
+    Moments r;
+    r.n = n;
+    r.mean = a.mean + delta * (b.n / n);
+    r.m2 = a.m2 + b.m2 + delta * delta * (a.n * b.n / n);
+    return r;
+}
+
+__device__ __forceinline__ Moments shfl_moments(Moments v, int o) {
+    Moments r;
+    r.n = __shfl_xor_sync(0xFFFFFFFFu, v.n, o);
+    r.mean = __shfl_xor_sync(0xFFFFFFFFu, v.mean, o);
+    r.m2 = __shfl_xor_sync(0xFFFFFFFFu, v.m2, o);
+    return r;
+}
+
+// Fixed-order block merge of per-thread moments (blockDim = kSelThreads).
+__device__ Moments block_merge(Moments v) {
+    __shared__ Moments s[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        Moments w = shfl_moments(v, o);
+        v = (lane & o) ? merge(w, v) : merge(v, w);
+    }
+    if (lane == 0) s[warp] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    if (warp == 0) {
+        v = lane < nw ? s[lane] : Moments{0.0, 0.0, 0.0};
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            Moments w = shfl_moments(v, o);
+            v = (lane & o) ? merge(w, v) : merge(v, w);
+        }
+    }
+    __syncthreads();
+    return v;  // valid in thread 0
+}
+
+// Compensated (sum, err) pair.  add() is Neumaier-style via TwoSum.
+struct CSum {
+    double s, e;
+    __device__ __forceinline__ void add(double x) {
+        double t, r;
+        two_sum(s, x, t, r);
+        s = t;
+        e += r;
+    }
+    __device__ __forceinline__ void add(CSum o) {
+        double t, r;
+        two_sum(s, o.s, t, r);
+        s = t;
+        e += o.e + r;
+    }
+};
+
+__device__ CSum block_csum(CSum v) {
+    __shared__ CSum s[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        CSum w{__shfl_xor_sync(0xFFFFFFFFu, v.s, o), __shfl_xor_sync(0xFFFFFFFFu, v.e, o)};
+        v.add(w);
+    }
+    if (lane == 0) s[warp] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    if (warp == 0) {
+        v = lane < nw ? s[lane] : CSum{0.0, 0.0};
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            CSum w{__shfl_xor_sync(0xFFFFFFFFu, v.s, o), __shfl_xor_sync(0xFFFFFFFFu, v.e, o)};
+            v.add(w);
+        }
+    }
+    __syncthreads();
+    return v;
+}
+
+__device__ __forceinline__ void chunk_of(int64_t C, int64_t& begin, int64_t& end) {
+    const int64_t chunk = (C + gridDim.x - 1) / gridDim.x;
+    begin = (int64_t)blockIdx.x * chunk;
+    end = begin + chunk < C ? begin + chunk : C;
+    if (begin > C) begin = C;
+}
+
+// True in every thread of the CTA that arrived last at `ticket`.  The
+// caller's global writes are fenced before arriving.
+__device__ bool last_to_arrive(uint32_t* ticket) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    return last;
+}
+
+}  // namespace
+
+// Reset the tree state of a run: level 1 is the full lattice.
+__global__ void zmc_init_state(State* st, int64_t level1_cells) {
+    uint32_t* w = reinterpret_cast<uint32_t*>(st);
+    for (size_t i = threadIdx.x; i < sizeof(State) / 4; i += blockDim.x) w[i] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) st->cells[1] = level1_cells;
+}
+
+// Step (b1): per cell the mean and sample spread (ddof 1) of the trial
+// estimates I_{c,t} = V S1 / n; over the level the mean mu and population
+// standard deviation sigma of the spreads; theta = mu + m sigma.
+__global__ void __launch_bounds__(kSelThreads)
+zmc_cell_stats(const Desc* __restrict__ desc, State* st, const double2* __restrict__ sums,
+               double2* __restrict__ cell_stats, double* part, int level) {
+    const Desc& D = *desc;
+    const int64_t C = st->cells[level];
+    if (C <= 0) return;
+    const int T = D.T;
+    const double V = D.volume[level];
+    const double n = (double)D.n;
+    int64_t begin, end;
+    chunk_of(C, begin, end);
+
+    Moments acc{0.0, 0.0, 0.0};
+    for (int64_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
+        const double2* row = sums + q * T;
+        double s = 0.0;
+        for (int t = 0; t < T; ++t) s += V * row[t].x / n;
+        const double mean = s / T;
+        double ss = 0.0;
+        for (int t = 0; t < T; ++t) {
+            const double e = V * row[t].x / n - mean;
+            ss += e * e;
+        }
+        const double spread = sqrt(ss / (T - 1));
+        cell_stats[q] = make_double2(mean, spread);
+        acc = merge(acc, Moments{1.0, spread, 0.0});
+    }
+    acc = block_merge(acc);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x + 0] = acc.n;
+        part[3 * blockIdx.x + 1] = acc.mean;
+        part[3 * blockIdx.x + 2] = acc.m2;
+    }
+    if (!last_to_arrive(&st->ticket[0])) return;
+
+    Moments all{0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        all = merge(all, Moments{__ldcg(part + 3 * b), __ldcg(part + 3 * b + 1),
+                                 __ldcg(part + 3 * b + 2)});
+    all = block_merge(all);
+    if (threadIdx.x == 0) {
+        const double mu = all.mean;
+        const double sigma = sqrt(all.m2 / all.n);
+        st->mu[level] = mu;
+        st->sigma[level] = sigma;
+        st->theta[level] = mu + D.m * sigma;
+        st->ticket[0] = 0u;
+    }
+}
+
+// Step (b2): flag cells whose spread is strictly larger than theta (never at
+// the last level), count them per CTA, and let the last CTA scan the counts,
+// apply the refinement budget and publish the next level's size.
+__global__ void __launch_bounds__(kSelThreads)
+zmc_flag_count(const Desc* __restrict__ desc, State* st, const double2* __restrict__ cell_stats,
+               int64_t* part_count, int64_t* part_offset, double* part_margin, int level) {
+    const Desc& D = *desc;
+    const int64_t C = st->cells[level];
+    if (C <= 0) return;
+    const double theta = st->theta[level];
+    const bool can_flag = level < D.depth;
+    int64_t begin, end;
+    chunk_of(C, begin, end);
+
+    int64_t cnt = 0;
+    double mm = INFINITY;
+    for (int64_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
+        const double s = cell_stats[q].y;
+        cnt += (can_flag && s > theta) ? 1 : 0;
+        if (theta > 0.0) mm = fmin(mm, fabs(s - theta) / theta);
+    }
+    __shared__ int64_t s_cnt[32];
+    __shared__ double s_mm[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+        mm = fmin(mm, __shfl_xor_sync(0xFFFFFFFFu, mm, o));
+    }
+    if (lane == 0) { s_cnt[warp] = cnt; s_mm[warp] = mm; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t c = 0;
+        double m = INFINITY;
+        for (int w = 0; w < nw; ++w) { c += s_cnt[w]; m = fmin(m, s_mm[w]); }
+        part_count[blockIdx.x] = c;
+        part_margin[blockIdx.x] = m;
+    }
+    if (!last_to_arrive(&st->ticket[1])) return;
+
+    // exclusive scan of the per-CTA counts (gridDim.x <= 32 * blockDim.x)
+    __shared__ int64_t s_off[kSelGrid];
+    __shared__ double s_m[kSelGrid];
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        double m = INFINITY;
+        for (int b = 0; b < (int)gridDim.x; ++b) {
+            s_off[b] = run;
+            run += __ldcg(part_count + b);
+            m = fmin(m, __ldcg(part_margin + b));
+        }
+        const int64_t F = run;
+        const int64_t per_cell = D.n * (int64_t)D.T;
+        const int64_t samples = st->samples + C * per_cell;
+        st->samples = samples;
+        int refine = 0;
+        int64_t flagged = F;
+        if (F > 0) {
+            const uint64_t next = (uint64_t)F * (uint64_t)D.K;
+            const int64_t room = (D.max_samples - samples) / per_cell;
+            if (next > (uint64_t)D.max_cells || next > (uint64_t)room ||
+                next > (uint64_t)D.cap_cells) {
+                atomicMax(&st->status, ZMC_ERR_BUDGET);
+                flagged = 0;
+            } else {
+                refine = 1;
+                st->cells[level + 1] = (int64_t)next;
+            }
+        }
+        st->flagged[level] = flagged;
+        st->refine[level] = refine;
+        st->min_margin[level] = can_flag ? m : INFINITY;
+        st->levels_run = level;
+        st->ticket[1] = 0u;
+        s_m[0] = m;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) part_offset[b] = s_off[b];
+}
+
+// Step (b3): write the coordinates of the flagged cells, in slot order, as
+// the next level's parent list (the children themselves are implicit:
+// child slot r*K + digit); add the accepted cells' mean and spread^2 / T to
+// this level's compensated partial sums.
+__global__ void __launch_bounds__(kSelThreads)
+zmc_compact(const Desc* __restrict__ desc, const State* __restrict__ st,
+            const double2* __restrict__ cell_stats, const int64_t* __restrict__ part_offset,
+            const uint32_t* __restrict__ parents_prev, uint32_t* __restrict__ parents_next,
+            double* __restrict__ part_acc, int level) {
+    const Desc& D = *desc;
+    const int64_t C = st->cells[level];
+    if (C <= 0) return;
+    const bool refine = st->refine[level] != 0;
+    const double theta = st->theta[level];
+    const int T = D.T, d = D.d;
+    int64_t begin, end;
+    chunk_of(C, begin, end);
+
+    __shared__ int s_warp[32];
+    __shared__ int s_total;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t offset = refine ? part_offset[blockIdx.x] : 0;
+    CSum val{0.0, 0.0}, var{0.0, 0.0};
+    for (int64_t q0 = begin; q0 < end; q0 += blockDim.x) {
+        const int64_t q = q0 + threadIdx.x;
+        const bool valid = q < end;
+        double2 ms = valid ? cell_stats[q] : make_double2(0.0, 0.0);
+        const bool flag = valid && refine && ms.y > theta;
+        const unsigned ballot = __ballot_sync(0xFFFFFFFFu, flag);
+        const int rank_in_warp = __popc(ballot & ((1u << lane) - 1u));
+        if (lane == 0) s_warp[warp] = __popc(ballot);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int w = 0; w < nw; ++w) { const int c = s_warp[w]; s_warp[w] = run; run += c; }
+            s_total = run;
+        }
+        __syncthreads();
+        if (flag) {
+            const int64_t r = offset + s_warp[warp] + rank_in_warp;
+            for (int i = 0; i < d; ++i)
+                parents_next[r * d + i] = (uint32_t)cell_coord(D, level, q, i, parents_prev);
+        } else if (valid) {
+            val.add(ms.x);
+            var.add(ms.y * ms.y / T);
+        }
+        offset += s_total;
+        __syncthreads();
+    }
+    val = block_csum(val);
+    var = block_csum(var);
+    if (threadIdx.x == 0) {
+        double* p = part_acc + ((size_t)level * gridDim.x + blockIdx.x) * 4;
+        p[0] = val.s; p[1] = val.e; p[2] = var.s; p[3] = var.e;
+    }
+}
+
+// Step (c): the compensated sum of every level's accepted partial sums, and
+// the result record.  One CTA.
+__global__ void __launch_bounds__(kSelThreads)
+zmc_final(const State* __restrict__ st, const double* __restrict__ part_acc, int sel_grid,
+          zmc_result* __restrict__ out) {
+    const int levels = st->levels_run;
+    CSum val{0.0, 0.0}, var{0.0, 0.0};
+    for (int L = 1; L <= levels; ++L) {
+        for (int b = threadIdx.x; b < sel_grid; b += blockDim.x) {
+            const double* p = part_acc + ((size_t)L * sel_grid + b) * 4;
+            val.add(CSum{p[0], p[1]});
+            var.add(CSum{p[2], p[3]});
+        }
+    }
+    val = block_csum(val);
+    var = block_csum(var);
+    if (threadIdx.x == 0) {
+        out->value = val.s + val.e;
+        out->std = sqrt(var.s + var.e);
+        int64_t cells = 0;
+        for (int L = 1; L <= ZMC_MAX_DEPTH; ++L) {
+            const bool ran = L <= levels;
+            out->cells_per_level[L - 1] = ran ? st->cells[L] : 0;
+            out->flagged_per_level[L - 1] = ran ? st->flagged[L] : 0;
+            out->theta_per_level[L - 1] = ran ? st->theta[L] : 0.0;
+            out->mu_per_level[L - 1] = ran ? st->mu[L] : 0.0;
+            out->sigma_per_level[L - 1] = ran ? st->sigma[L] : 0.0;
+            out->min_margin_per_level[L - 1] = ran ? st->min_margin[L] : 0.0;
+            if (ran) cells += st->cells[L];
+        }
+        out->cells_evaluated = cells;
+        out->samples = st->samples;
+        out->levels_run = levels;
+        out->status = st->status;
+    }
+}
+
+// Philox words for bit-exact checks of the generator used by kernel (a).
+__global__ void zmc_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1,
+                                uint32_t c2, uint32_t c3, int64_t count, uint4* out) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < count;
+         b += (int64_t)gridDim.x * blockDim.x)
+        out[b] = philox4x32_10(make_uint4(c0 + (uint32_t)b, c1, c2, c3), k0, k1);
+}
+
+// ------------------------------------------------------------- launchers
+
+cudaError_t launch_init(const Buffers& b, int64_t level1_cells, cudaStream_t s) {
+    zmc_init_state<<<1, 256, 0, s>>>(b.state, level1_cells);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select(const Buffers& b, int level, const uint32_t* parents_prev,
+                          uint32_t* parents_next, cudaStream_t s) {
+    zmc_cell_stats<<<kSelGrid, kSelThreads, 0, s>>>(b.desc, b.state, b.sums, b.cell_stats,
+                                                    b.part_stats, level);
+    zmc_flag_count<<<kSelGrid, kSelThreads, 0, s>>>(b.desc, b.state, b.cell_stats,
+                                                    b.part_count, b.part_offset,
+                                                    b.part_margin, level);
+    zmc_compact<<<kSelGrid, kSelThreads, 0, s>>>(b.desc, b.state, b.cell_stats, b.part_offset,
+                                                 parents_prev, parents_next, b.part_acc, level);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final(const Buffers& b, cudaStream_t s) {
+    zmc_final<<<1, kSelThreads, 0, s>>>(b.state, b.part_acc, kSelGrid, b.result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                          uint32_t c3, int64_t count, uint32_t* out, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    zmc_philox_fill<<<(int)blocks, 256, 0, s>>>((uint32_t)(seed & 0xFFFFFFFFu),
+                                               (uint32_t)(seed >> 32), c0, c1, c2, c3,
+                                               count, reinterpret_cast<uint4*>(out));
+    return cudaGetLastError();
+}
+
+}  // namespace zmc

@@ -1,0 +1,50 @@
+// Host-side declarations shared by the translation units of libzmc: the
+// device buffers of a handle and the kernel launchers.  Not part of the
+// public ABI (include/zmc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "zmc_layout.h"
+
+namespace zmc {
+
+// Device buffers of one handle.
+struct Buffers {
+    Desc* desc;
+    State* state;
+    double2* sums;        // [cap_cells * T]   (S1, S2) per (cell, trial)
+    double2* cell_stats;  // [cap_cells]       (mean, spread)
+    uint32_t* parents[2]; // [cap_parents * d] flagged cells, ping-pong
+    double* part_stats;   // [kSelGrid * 3]    (count, mean, M2)
+    int64_t* part_count;  // [kSelGrid]
+    int64_t* part_offset; // [kSelGrid]
+    double* part_margin;  // [kSelGrid]
+    double* part_acc;     // [(ZMC_MAX_DEPTH + 1) * kSelGrid * 4]
+    zmc_result* result;
+};
+
+// Selection kernels run on a fixed grid so that their reduction order, and
+// hence every bit of the result, does not depend on the GPU's SM count.
+constexpr int kSelGrid = 256;
+constexpr int kSelThreads = 256;
+
+// Launch shape of the sampling kernel.
+struct EvalShape {
+    int threads;   // per CTA, multiple of 32, <= 1024
+    int grid;      // persistent CTAs
+};
+
+// Kernels (b): per-cell statistics + threshold, flag + count, compaction.
+cudaError_t launch_init(const Buffers& b, int64_t level1_cells, cudaStream_t s);
+cudaError_t launch_select(const Buffers& b, int level, const uint32_t* parents_prev,
+                          uint32_t* parents_next, cudaStream_t s);
+// Kernel (c): compensated final reduction into the result.
+cudaError_t launch_final(const Buffers& b, cudaStream_t s);
+
+cudaError_t launch_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                          uint32_t c3, int64_t count, uint32_t* out,
+                          cudaStream_t s);
+
+}  // namespace zmc

@@ -1,0 +1,65 @@
+// Memory layout shared by the host code and every kernel of libzmc,
+// including the kernels compiled at run time for expression integrands
+// (hence no CUDA runtime header here).  Not part of the public ABI.
+#pragma once
+
+#ifndef __CUDACC_RTC__
+#include <stdint.h>
+#endif
+#include "../../include/zmc.h"
+
+namespace zmc {
+
+constexpr int kMaxParams = 2 * ZMC_MAX_DIM + 2;
+
+// Integrand registry ids (the order is internal to the CUDA path).
+enum Integrand : int32_t {
+    kConstant = 0,
+    kLinear = 1,
+    kSinSum = 2,
+    kGaussNorm = 3,
+    kGenzOsc = 4,
+    kGenzProdPeak = 5,
+    kGenzGauss = 6,
+    kGenzCorner = 7,
+    kNumIntegrands = 8,
+    kExpression = 100,
+};
+
+// Everything the kernels need to know about one integration, uploaded to
+// device memory before each run.  Plain old data, host-computed.
+struct Desc {
+    int32_t d, k, T, depth;
+    int32_t integrand, mode;
+    int64_t n;                       // points per (cell, trial)
+    int64_t K;                       // k^d children per split cell
+    int64_t kpow[ZMC_MAX_DIM];       // k^i
+    uint32_t key[2];                 // Philox key = (seed lo, seed hi)
+    double m;                        // sigma multiplier
+    int64_t max_cells, max_samples;  // refinement budget
+    int64_t cap_cells;               // capacity of the per-level buffers
+    double lo[ZMC_MAX_DIM];
+    double width[ZMC_MAX_DEPTH + 1][ZMC_MAX_DIM];  // (hi - lo) / k^L
+    double volume[ZMC_MAX_DEPTH + 1];              // prod_i width[L][i]
+    // Per-dimension integrand parameters (pa, pb) and scalars (c[0..3]),
+    // rearranged on the host from the user's parameter list.
+    double pa[ZMC_MAX_DIM], pb[ZMC_MAX_DIM];
+    double c[4];
+};
+
+// Tree state of one run, written only by the kernels.  Index L = level.
+struct State {
+    int64_t cells[ZMC_MAX_DEPTH + 2];
+    int64_t flagged[ZMC_MAX_DEPTH + 2];
+    double mu[ZMC_MAX_DEPTH + 2];
+    double sigma[ZMC_MAX_DEPTH + 2];
+    double theta[ZMC_MAX_DEPTH + 2];
+    double min_margin[ZMC_MAX_DEPTH + 2];
+    int32_t refine[ZMC_MAX_DEPTH + 2];
+    int64_t samples;
+    int32_t status;      // ZMC_OK or a ZMC_ERR_* code
+    int32_t levels_run;
+    uint32_t ticket[4];  // last-block arrival counters (self-resetting)
+};
+
+}  // namespace zmc

@@ -1,0 +1,97 @@
+"""The C ABI library loads without a GPU, exports every entry point that
+include/zmc.h declares, and validates arguments on the host."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "zmc.h")
+
+
+@pytest.fixture(scope="module")
+def zmc():
+    from paper_1902_07916_gb300 import build
+    build.build()
+    from paper_1902_07916_gb300 import zmc as mod
+    return mod
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"ZMC_API\s+[\w\s\*]+?\b(zmc_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_abi():
+    names = declared_symbols()
+    for must in ["zmc_create", "zmc_set_integrand", "zmc_set_precision", "zmc_set_limits",
+                 "zmc_integrate", "zmc_enqueue", "zmc_read_result", "zmc_integrate_batch",
+                 "zmc_last_error", "zmc_destroy", "zmc_philox_words", "zmc_set_trace",
+                 "zmc_trace_level"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(zmc):
+    lib = ctypes.CDLL(zmc.LIB_PATH)
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_result_struct_matches_header(zmc):
+    # 2 doubles, 2 int64, 2 int32, then 6 arrays of 16 eight-byte values
+    assert ctypes.sizeof(zmc.zmc_result) == 16 + 16 + 8 + 6 * 16 * 8
+
+
+@pytest.mark.parametrize("kw,bad", [
+    ({"dim": 0}, "dim"), ({"dim": 17}, "dim"), ({"k": 1}, "k"), ({"n": 1}, "n"),
+    ({"num_trials": 1}, "num_trials"), ({"depth": 0}, "depth"), ({"depth": 17}, "depth"),
+    ({"sigma_multiplier": -1.0}, "sigma"), ({"sigma_multiplier": float("nan")}, "sigma"),
+    ({"hi": [0.0, 1.0]}, "lo"), ({"k": 70000}, "k^dim"),
+])
+def test_create_rejects_bad_arguments(zmc, kw, bad):
+    args = dict(dim=2, lo=[0.0, 0.0], hi=[1.0, 1.0], k=3, n=100, num_trials=4, depth=2,
+                sigma_multiplier=1.0, seed=1)
+    args.update(kw)
+    if "dim" in kw and kw["dim"] > 0:
+        args["lo"] = [0.0] * kw["dim"]
+        args["hi"] = [1.0] * kw["dim"]
+    with pytest.raises(zmc.ZmcError) as e:
+        zmc.zmc_create(**args)
+    assert e.value.code == zmc.ZMC_ERR_ARG
+    assert bad.split("^")[0] in zmc.zmc_last_error(None)
+
+
+def test_integrand_validation_on_host(zmc):
+    h = zmc.zmc_create(3, [0.0] * 3, [1.0] * 3, 2, 16, 2, 1, 0.0, 0)
+    try:
+        with pytest.raises(zmc.ZmcError) as e:
+            zmc.zmc_set_integrand(h, "no_such_integrand")
+        assert e.value.code == zmc.ZMC_ERR_ARG
+        with pytest.raises(zmc.ZmcError) as e:
+            zmc.zmc_set_integrand(h, "genz_gauss", [1.0, 2.0])   # needs 2*dim
+        assert "takes 6 parameters" in zmc.zmc_last_error(h)
+        with pytest.raises(zmc.ZmcError):
+            zmc.zmc_set_integrand(h, "gauss_norm", [-0.1])
+        with pytest.raises(zmc.ZmcError):
+            zmc.zmc_set_integrand(h, "constant", [float("inf")])
+        with pytest.raises(zmc.ZmcError):
+            zmc.zmc_set_integrand(h, "expr:x[0]; }")            # not one expression
+        zmc.zmc_set_integrand(h, "genz_corner", [1.0, 2.0, 3.0])
+        with pytest.raises(zmc.ZmcError):
+            zmc.zmc_set_precision(h, 7)
+        with pytest.raises(zmc.ZmcError):
+            zmc.zmc_set_limits(h, 7, 1 << 40)                   # below level 1 (8 cells)
+        zmc.zmc_set_limits(h, 8, 8 * 16 * 2)
+    finally:
+        zmc.zmc_destroy(h)
+
+
+def test_integrate_without_integrand_reports_it(zmc):
+    h = zmc.zmc_create(1, [0.0], [1.0], 2, 16, 2, 1, 0.0, 0)
+    try:
+        with pytest.raises(zmc.ZmcError) as e:
+            zmc.zmc_integrate(h)
+        assert e.value.code == zmc.ZMC_ERR_NOINTEGRAND
+    finally:
+        zmc.zmc_destroy(h)

@@ -1,0 +1,154 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 mode: Philox words bit-exact; per-(cell, trial) sums within 1e-12
+relative; identical selection decisions (same flagged cells, same order);
+final value and error within 1e-10 relative.  FP32 modes: per-(cell, trial)
+sums within the FP32 evaluation tolerance of the oracle run on the same
+(23-bit) uniforms, decisions consistent with the kernel's own statistics, and
+the value within 4 standard deviations of the closed form.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import closed_forms as CF
+from oracle import zmc_oracle as O
+from paper_1902_07916_gb300.workloads import Workload, sin3d
+
+from parity import (check_decisions_consistent, compare_fp64, run_gpu, run_oracle,
+                    sums_tolerance)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def zmc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1902_07916_gb300 import build
+    build.build()
+    from paper_1902_07916_gb300 import zmc as mod
+    return mod
+
+
+# ------------------------------------------------------------- generator
+
+@pytest.mark.parametrize("seed,ctr", [
+    (0, (0, 0, 0, 0)), (0x123456789ABCDEF0, (7, 3, 11, 2)),
+    (2**64 - 1, (0xFFFFFFF0, 0xFFFFFFFF, 0xFFFFFFFF, 0xFFFFFFFF)),
+    (42, (1 << 31, 5, 4095, 1)),
+])
+def test_philox_words_bit_exact(zmc, seed, ctr):
+    import torch
+    count = 1000   # crosses the 2^32 wrap of counter word 0 for the third case
+    out = torch.zeros(4 * count, dtype=torch.int32, device="cuda")
+    zmc.zmc_philox_words(seed, *ctr, count, out.data_ptr(),
+                         torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32).reshape(count, 4)
+    key = O.seed_key(seed)
+    for b in list(range(0, count, 37)) + [count - 1]:
+        c = ((ctr[0] + b) & 0xFFFFFFFF, ctr[1], ctr[2], ctr[3])
+        assert np.array_equal(got[b], O.philox4x32_10(c, key)), b
+
+
+# ---------------------------------------------------- FP64 full parity
+
+def W(name, integrand, d, a, b, k, n, T, depth, m, seed, params=(), **kw):
+    return Workload(name, integrand, d, [a] * d, [b] * d, k, n, T, depth, m, seed,
+                    list(params), **kw)
+
+
+FP64_CASES = [
+    sin3d(),
+    W("sin1d_ragged", "sin_sum", 1, -2.0, 3.0, 5, 7, 3, 3, 0.5, 11),
+    W("gauss2_n2", "genz_gauss", 2, 0.0, 1.0, 3, 2, 2, 4, 0.0, 5, [6.0, 3.0, 0.4, 0.7]),
+    W("corner5", "genz_corner", 5, 0.0, 1.0, 2, 33, 4, 3, 0.5, 3, [1.0, 2.0, 3.0, 4.0, 5.0]),
+    W("linear16", "linear", 16, -1.0, 1.0, 2, 9, 2, 1, 1.0, 9,
+      [0.5] + [0.1 * i for i in range(16)]),
+    W("prodpeak4", "genz_prodpeak", 4, 0.0, 1.0, 3, 101, 6, 3, 1.0, 4,
+      [5.0, 7.0, 2.0, 9.0, 0.3, 0.5, 0.7, 0.1]),
+    W("gaussnorm3", "gauss_norm", 3, -1.0, 1.0, 4, 64, 4, 3, 1.0, 8, [0.2]),
+    W("osc3", "genz_osc", 3, 0.0, 1.0, 3, 50, 5, 3, 0.8, 6, [0.3, 4.0, 8.0, 2.0]),
+    W("sin6_tiles", "sin_sum", 6, 0.0, 10.0, 4, 256, 10, 2, 1.5, 2),
+]
+
+
+@pytest.mark.parametrize("w", FP64_CASES, ids=[w.name for w in FP64_CASES])
+def test_fp64_matches_oracle(zmc, w):
+    res, levels = run_gpu(zmc, w, "fp64")
+    ref = run_oracle(w)
+    compare_fp64(w, res, levels, ref)
+
+
+def test_fp64_graph_replay_matches_trace(zmc):
+    # The production path (captured graph, no per-level sync) gives bit-for-bit
+    # the result of the traced path, run after run.
+    w = FP64_CASES[3]
+    traced, _ = run_gpu(zmc, w, "fp64", trace=True)
+    it = zmc.Integrator(w.dim, w.lo, w.hi, w.k, w.n, w.trials, w.depth, w.sigma_multiplier,
+                        w.seed, w.integrand, w.params)
+    try:
+        for _ in range(3):
+            r = it.integrate()
+            assert (r.value, r.std, r.flagged_per_level) == (
+                traced.value, traced.std, traced.flagged_per_level)
+    finally:
+        it.close()
+
+
+def test_constant_integrand_exact(zmc):
+    w = W("const", "constant", 3, 0.0, 10.0, 4, 1000, 5, 3, 2.0, 7, [2.5])
+    for prec in ("fp64", "fp32_fp64acc", "fp32_kahan"):
+        res, _ = run_gpu(zmc, w, prec, trace=False)
+        assert res.value == 2500.0 and res.std == 0.0, prec
+        assert res.levels_run == 1 and res.flagged_per_level == [0]
+
+
+def test_budget_rule_matches_oracle(zmc):
+    base = W("budget", "genz_gauss", 2, 0.0, 1.0, 3, 50, 4, 3, 0.0, 11, [6.0, 6.0, 0.5, 0.5])
+    free = run_oracle(base)
+    assert free.flagged_per_level[0] > 0
+    for kw in ({"max_cells": free.flagged_per_level[0] * 9 - 1},
+               {"max_samples": 9 * 50 * 4 + 1}):
+        w = base.with_(**kw)
+        res, levels = run_gpu(zmc, w, "fp64")
+        ref = run_oracle(w)
+        assert ref.status == O.STATUS_BUDGET
+        assert res.status == zmc.ZMC_ERR_BUDGET
+        compare_fp64(w, res, levels, ref)
+
+
+def test_nonfinite_integrand_is_reported(zmc):
+    # (sqrt(2 pi) s)^-d overflows for s = 1e-200 and exp(...) underflows: inf * 0
+    w = W("nan", "gauss_norm", 3, -1.0, 1.0, 2, 16, 2, 2, 1.0, 1, [1e-200])
+    res, _ = run_gpu(zmc, w, "fp64", trace=False)
+    assert res.status == zmc.ZMC_ERR_NONFINITE
+
+
+# ---------------------------------------------------------- FP32 modes
+
+FP32_CASES = [
+    (sin3d(), None),
+    (W("gaussnorm3", "gauss_norm", 3, -1.0, 1.0, 4, 256, 6, 3, 1.0, 8, [0.2]), None),
+    (W("corner5", "genz_corner", 5, 0.0, 1.0, 2, 129, 8, 2, 0.5, 3, [1.0, 2.0, 3.0, 4.0, 5.0]),
+     None),
+    (W("prodpeak3", "genz_prodpeak", 3, 0.0, 1.0, 3, 257, 6, 2, 1.0, 4,
+       [5.0, 7.0, 2.0, 0.3, 0.5, 0.7]), None),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp32_fp64acc", "fp32_kahan"])
+@pytest.mark.parametrize("w,_", FP32_CASES, ids=[c[0].name for c in FP32_CASES])
+def test_fp32_modes_within_stated_tolerance(zmc, w, _, prec):
+    res, levels = run_gpu(zmc, w, prec)
+    ref = run_oracle(w, fp32_uniforms=True)
+    # level-1 sums: FP32 points and integrand against FP64 on the same uniforms
+    g, r = levels[0], ref.levels[0]
+    err = np.abs(g["sums"] - r.sums)
+    assert np.all(err <= sums_tolerance(r.sums, w.n, 2e-5)), float(err.max())
+    check_decisions_consistent(w, levels, res)
+    exact = CF.integral(w.integrand, w.lo, w.hi, w.params)
+    assert abs(res.value - exact) <= 4 * res.std + 1e-6 * abs(exact), (res.value, exact, res.std)
