@@ -1,0 +1,397 @@
+"""Benchmark: stratified Monte Carlo integration with heuristic tree search.
+
+One step = one whole integration (every level of the tree: sampling kernel,
+selection kernels, final reduction) of the 6-D oscillating integrand
+sin(x1+...+x6) on [0,10]^6 with k=4 (4096 cells), n=2^16 points per cell and
+trial, 10 trials, depth 3, sigma multiplier 1.5, in the FP32-evaluation /
+FP64-accumulation mode, under the library's default budget (2^24 cells per
+level, 2^40 points per run).  The metric is points evaluated per second
+(Gsamples/s).  Inputs are synthetic: the integrand is a formula.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the from-scratch reference of
+the method) on the host cores, on a bounded sample of the same workload.
+Under torchrun every rank integrates its own independent problem (seed +
+rank): weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gsamples/s per GB300 (stratified MC + tree search, sin(sum x) 6-D)"
+UNIT = "Gsamples/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="sin6d")
+    p.add_argument("--precision", default="fp32_fp64acc")
+    p.add_argument("--n", type=int, default=None, help="override points per cell (small "
+                   "profiling cases only; the bench line is invalid with it)")
+    p.add_argument("--depth", type=int, default=None, help="override depth (profiling only)")
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    return p.parse_args()
+
+
+def workload(args):
+    from paper_1902_07916_gb300 import workloads
+    w = workloads.WORKLOADS[args.workload]()
+    if args.n is not None:
+        w = w.with_(n=args.n)
+    if args.depth is not None:
+        w = w.with_(depth=args.depth)
+    return w
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------- our arm
+
+def philox_multiplies_per_sample(d: int) -> float:
+    """Algorithmic integer work per point: one Philox4x32-10 block per four
+    points and dimension, ten rounds of two 32x32->64-bit products, each
+    product counted as two 32-bit multiply results (high and low half)."""
+    return d / 4.0 * 10 * 2 * 2
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1902_07916_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1902_07916_gb300 import zmc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    w = workload(args)
+    seed = w.seed + rank
+    prec = zmc.PRECISIONS[args.precision]
+    it = zmc.Integrator(w.dim, w.lo, w.hi, w.k, w.n, w.trials, w.depth, w.sigma_multiplier,
+                        seed, w.integrand, w.params, precision=prec)
+    zmc.zmc_set_profiling(it.h, True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    for _ in range(max(args.warmup, 0)):
+        it.enqueue(stream)
+    torch.cuda.synchronize(dev)
+    kernels_per_run, h2d_bytes, d2h_bytes = zmc.zmc_run_info(it.h)
+
+    step_ms, eval_ms, samples, results = [], [], [], []
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it.enqueue(stream)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            per_level, _ = zmc.zmc_profile(it.h, w.depth)
+            eval_ms.append(sum(per_level))
+            r = it.read_result(stream)
+            samples.append(r.samples)
+            results.append(r)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.summary()
+
+    total_ms = sum(step_ms)
+    t_max = allreduce_max(world, total_ms)
+    all_samples = allreduce_sum(world, float(sum(samples)))
+    value = all_samples / (t_max * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (the sampling kernel)
+    ops = sum(samples) * philox_multiplies_per_sample(w.dim)
+    eval_s = sum(eval_ms) * 1e-3
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = clk.get("sm_max_mhz") or 2070.0
+    peak = 64 * sms * max_mhz * 1e6 / 1e12           # T int32-multiply results / s
+    achieved = ops / eval_s / 1e12
+
+    # end to end: the public call with host result, per step
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = it.integrate(stream)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_value = allreduce_sum(world, float(r.samples * len(e2e_t))) / allreduce_max(
+        world, sum(e2e_t)) / 1e9
+
+    fp64 = None
+    if not args.no_fp64 and rank == 0 and prec != zmc.ZMC_FP64:
+        it64 = zmc.Integrator(w.dim, w.lo, w.hi, w.k, w.n, w.trials, w.depth,
+                              w.sigma_multiplier, seed, w.integrand, w.params,
+                              precision=zmc.ZMC_FP64)
+        it64.enqueue(stream)                      # warm-up (graph capture)
+        torch.cuda.synchronize(dev)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it64.enqueue(stream)
+        e1.record(stream)
+        r64 = it64.read_result(stream)
+        ms64 = e0.elapsed_time(e1)
+        it64.close()
+        ref = results[-1]
+        fp64 = {"value": r64.samples / (ms64 * 1e-3) / 1e9, "unit": UNIT, "steps": 1,
+                "warmup": 1, "speedup_of_headline": value / (r64.samples / (ms64 * 1e-3) / 1e9),
+                "result": r64.value, "std": r64.std,
+                "headline_minus_fp64_over_std": (ref.value - r64.value) / r64.std
+                if r64.std > 0 else None,
+                "levels_run": r64.levels_run, "flagged_per_level": r64.flagged_per_level}
+    it.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w, target_s=12.0)
+
+    if rank != 0:
+        return None
+    r = results[-1]
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_max / max(args.steps, 1), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 eval / f64 accum" if prec == zmc.ZMC_FP32_FP64ACC else args.precision,
+        "data": "synthetic (analytic integrand, Philox counter-based points)",
+        "config": {
+            "workload": "%s: sin(sum x) on [0,10]^%d, k=%d, n=%d, trials=%d, depth=%d, m=%g, "
+                        "budget 2^24 cells/level, 2^40 points/run" % (
+                            w.name, w.dim, w.k, w.n, w.trials, w.depth, w.sigma_multiplier),
+            "precision": args.precision, "seed": w.seed, "parallelism": "replicas x%d" % world,
+            "l2": "flushed between steps (256 MiB write, outside the timed events)",
+            "samples_per_step": r.samples, "levels_run": r.levels_run,
+            "cells_per_level": r.cells_per_level, "flagged_per_level": r.flagged_per_level,
+            "status": r.status, "result": r.value, "std": r.std,
+        },
+        "roofline": {
+            "bound": "alu", "kernel": "zmc_eval_reduce (fused Philox/evaluate/reduce)",
+            "achieved": round(achieved, 3), "peak": round(peak, 3),
+            "unit": "T int32-multiply results/s",
+            "frac": round(achieved / peak, 4),
+            "peak_basis": "64 IMAD lanes/clk/SM x %d SMs x %.0f MHz (max SM clock)" % (
+                sms, max_mhz),
+            "work_per_sample": philox_multiplies_per_sample(w.dim),
+            "kernel_ms_per_step": round(sum(eval_ms) / len(eval_ms), 3),
+            "kernel_share_of_step": round(sum(eval_ms) / total_ms, 4),
+            "traffic": None,
+        },
+        "clocks": clk,
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
+                "d2h_bytes_per_step": d2h_bytes},
+        "gpu_launches": kernels_per_run * args.steps,
+        "fp64": fp64,
+        "cpu_baseline": cpu,
+    }
+    return line
+
+
+# ------------------------------------------------------ CPU baseline
+
+def cpu_baseline(w, target_s: float = 12.0, max_cells: int | None = None):
+    """The FP64 oracle on the host cores: level-1 (cell, trial) sums of the
+    first M cells of the workload, M doubled until the run takes target_s."""
+    import numpy as np
+    from oracle import zmc_oracle as O
+    threads = O.default_threads()
+    coords_all = O.level1_cells(w.k, w.dim)
+    M = 1
+    limit = max_cells or coords_all.shape[0]
+    while True:
+        t0 = time.perf_counter()
+        O.cell_sums(w.seed, 1, w.lo, w.hi, w.k, w.n, w.trials, w.integrand, w.params,
+                    np.arange(M), coords_all[:M], threads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or M >= limit:
+            break
+        M = min(limit, max(M * 2, int(M * target_s / max(dt, 1e-3) * 1.1)))
+    samples = M * w.trials * w.n
+    return {"value": round(samples / dt / 1e9, 5), "unit": UNIT, "cores": threads,
+            "kind": "oracle",
+            "sample": "level-1 sums of the first %d of %d cells x %d trials x %d points "
+                      "(%.3g points, %.1f s)" % (M, coords_all.shape[0], w.trials, w.n,
+                                                  samples, dt)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    import numpy as np
+    from oracle import zmc_oracle as O
+    w = workload(args)
+    threads = O.default_threads()
+    coords_all = O.level1_cells(w.k, w.dim)
+    # each step: a bounded sample of level-1 cells, sized to ~2 s on the host
+    M = 1
+    while True:
+        t0 = time.perf_counter()
+        O.cell_sums(w.seed, 1, w.lo, w.hi, w.k, w.n, w.trials, w.integrand, w.params,
+                    np.arange(M), coords_all[:M], threads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= 1.0 or M >= coords_all.shape[0]:
+            break
+        M = min(coords_all.shape[0], max(2 * M, int(M * 2.0 / max(dt, 1e-3))))
+    for _ in range(args.warmup):
+        O.cell_sums(w.seed, 1, w.lo, w.hi, w.k, w.n, w.trials, w.integrand, w.params,
+                    np.arange(M), coords_all[:M], threads=threads)
+    times = []
+    for s in range(args.steps):
+        lo_c = (s * M) % coords_all.shape[0]
+        idx = (np.arange(M) + lo_c) % coords_all.shape[0]
+        t0 = time.perf_counter()
+        O.cell_sums(w.seed, 1, w.lo, w.hi, w.k, w.n, w.trials, w.integrand, w.params,
+                    idx, coords_all[idx], threads=threads)
+        times.append(time.perf_counter() - t0)
+    samples = M * w.trials * w.n
+    value = samples * len(times) / sum(times) / 1e9
+    sample = ("per step: level-1 sums of %d cells x %d trials x %d points (%.3g points)"
+              % (M, w.trials, w.n, samples))
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * sum(times) / len(times), 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (analytic integrand, Philox counter-based points)",
+        "config": {"workload": "%s (CPU oracle, bounded sample)" % w.name,
+                   "precision": "fp64"},
+        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    try:
+        if args.impl == "reference":
+            line = run_reference(args, world, rank)
+        else:
+            line = run_ours(args, world, rank, local)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

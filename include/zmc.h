@@ -214,6 +214,23 @@ ZMC_API int zmc_philox_words(uint64_t seed, uint32_t c0, uint32_t c1,
                              uint32_t c2, uint32_t c3, int64_t count,
                              uint32_t* out, void* stream);
 
+/*
+ * Instrumentation for measurement.
+ * zmc_set_profiling(h, 1): later runs record CUDA events around every
+ * level's sampling kernel (inside the captured graph, on the run's stream).
+ * zmc_profile(h, eval_ms, levels) then writes, after the stream has passed
+ * the run, the sampling kernel's duration per level (host double[depth]) and
+ * the number of levels that had cells to *levels.
+ * zmc_run_info(h, kernels, h2d_bytes, d2h_bytes): kernels launched by one
+ * run (the kernel nodes of the captured graph), and the bytes zmc_integrate
+ * copies host->device (the run's parameters) and device->host (the result)
+ * per call.  Any pointer may be NULL.  Errors: ZMC_ERR_ARG, ZMC_ERR_CUDA.
+ */
+ZMC_API int zmc_set_profiling(zmc_handle h, int on);
+ZMC_API int zmc_profile(zmc_handle h, double* eval_ms, int* levels);
+ZMC_API int zmc_run_info(zmc_handle h, int64_t* kernels, int64_t* h2d_bytes,
+                         int64_t* d2h_bytes);
+
 /* zmc_last_error -- message of the last failed call on h (or of the last
  * failed zmc_create / handle-less call when h is NULL).  Never NULL; valid
  * until the next call on the same handle. */

@@ -15,9 +15,9 @@
 #include "zmc_internal.h"
 
 namespace zmc {
-const void* eval_kernel_fp64(int fn);
-const void* eval_kernel_fp32_fp64acc(int fn);
-const void* eval_kernel_fp32_kahan(int fn);
+const void* eval_kernel_fp64(int fn, bool wide);
+const void* eval_kernel_fp32_fp64acc(int fn, bool wide);
+const void* eval_kernel_fp32_kahan(int fn, bool wide);
 cudaError_t launch_batch(int count, zmc_handle const* hs, cudaStream_t s);
 }  // namespace zmc
 
@@ -61,6 +61,9 @@ struct zmc_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool graph_stale = true;
+    int64_t graph_kernels = 0;
+    bool profiling = false;
+    cudaEvent_t ev[ZMC_MAX_DEPTH + 1][2] = {};  // around each level's sampling kernel
 };
 
 namespace {
@@ -174,6 +177,11 @@ void free_device(zmc_ctx* h) {
     h->graph = nullptr;
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->cap_stream = nullptr;
+    for (auto& pair : h->ev)
+        for (cudaEvent_t& e : pair) {
+            if (e) cudaEventDestroy(e);
+            e = nullptr;
+        }
     Buffers& b = h->buf;
     void* ptrs[] = {b.desc, b.state, b.sums, b.cell_stats, b.parents[0], b.parents[1],
                     b.part_stats, b.part_count, b.part_offset, b.part_margin, b.part_acc,
@@ -286,12 +294,28 @@ void build_desc(const zmc_ctx* h, Desc& D) {
     }
 }
 
+// Bound on |argument| of the sine / cosine over the box, for the FP32
+// kernels' choice between the bounded and the any-argument reduction.
+double trig_argument_bound(const zmc_ctx* h) {
+    double b = 0.0;
+    for (int i = 0; i < h->dim; ++i) {
+        const double r = std::max(fabs(h->lo[i]), fabs(h->hi[i]));
+        if (h->integrand == kSinSum) b += r;
+        else if (h->integrand == kGenzOsc) b += fabs(h->params[1 + i]) * r;
+    }
+    if (h->integrand == kGenzOsc) b += fabs(2.0 * M_PI * h->params[0]);
+    return b;
+}
+
 const void* eval_kernel(const zmc_ctx* h) {
     if (h->integrand == kExpression) return h->jit.kernel;
+    // 8192 is the FP32 reduction's limit; the margin covers FP32 rounding of
+    // the accumulated argument.
+    const bool wide = trig_argument_bound(h) > 0.99 * 8192.0;
     switch (h->mode) {
-    case ZMC_FP64: return eval_kernel_fp64(h->integrand);
-    case ZMC_FP32_FP64ACC: return eval_kernel_fp32_fp64acc(h->integrand);
-    default: return eval_kernel_fp32_kahan(h->integrand);
+    case ZMC_FP64: return eval_kernel_fp64(h->integrand, wide);
+    case ZMC_FP32_FP64ACC: return eval_kernel_fp32_fp64acc(h->integrand, wide);
+    default: return eval_kernel_fp32_kahan(h->integrand, wide);
     }
 }
 
@@ -318,8 +342,9 @@ void plan_shapes(zmc_ctx* h) {
 cudaError_t enqueue_eval(zmc_ctx* h, int level, const uint32_t* parents_prev, cudaStream_t s) {
     const EvalShape sh = h->shapes[level];
     const Buffers& b = h->buf;
+    const PhiloxKeys keys = philox_keys(h->seed);
     void* args[] = {(void*)&b.desc, (void*)&b.state, (void*)&parents_prev, (void*)&b.sums,
-                    (void*)&level};
+                    (void*)&level, (void*)&keys};
     return cudaLaunchKernel(eval_kernel(h), dim3(sh.grid), dim3(sh.threads), args, 0, s);
 }
 
@@ -337,8 +362,10 @@ cudaError_t enqueue_levels(zmc_ctx* h, cudaStream_t s, int only_level = 0) {
     for (int L = first; L <= last; ++L) {
         const uint32_t* prev = b.parents[L & 1];       // written by level L-1
         uint32_t* next = b.parents[(L + 1) & 1];
+        if (h->profiling && (e = cudaEventRecordWithFlags(h->ev[L][0], s, cudaEventRecordExternal)) != cudaSuccess) return e;
         e = enqueue_eval(h, L, prev, s);
         if (e != cudaSuccess) return e;
+        if (h->profiling && (e = cudaEventRecordWithFlags(h->ev[L][1], s, cudaEventRecordExternal)) != cudaSuccess) return e;
         e = launch_select(b, L, prev, next, s);
         if (e != cudaSuccess) return e;
     }
@@ -355,11 +382,23 @@ int upload_desc(zmc_ctx* h, cudaStream_t s) {
     return ZMC_OK;
 }
 
+int ensure_events(zmc_ctx* h) {
+    if (!h->profiling) return ZMC_OK;
+    for (int L = 1; L <= h->depth; ++L)
+        for (cudaEvent_t& ev : h->ev[L])
+            if (!ev) {
+                cudaError_t e = cudaEventCreate(&ev);
+                if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
+            }
+    return ZMC_OK;
+}
+
 int ensure_graph(zmc_ctx* h) {
     if (!h->graph_stale && h->graph) return ZMC_OK;
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
     plan_shapes(h);
+    if (int rc = ensure_events(h)) return rc;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
@@ -370,6 +409,16 @@ int ensure_graph(zmc_ctx* h) {
         return cuda_fail(h, le, "kernel launch during capture");
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    h->graph_kernels = 0;
+    for (cudaGraphNode_t node : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(node, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+            ++h->graph_kernels;
+    }
     e = cudaGraphInstantiate(&h->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
@@ -395,6 +444,7 @@ int finish_result(zmc_ctx* h, zmc_result* out) {
 int run_traced(zmc_ctx* h, cudaStream_t s) {
     h->trace_levels.clear();
     plan_shapes(h);
+    if (int rc = ensure_events(h)) return rc;
     cudaError_t e = cudaSuccess;
     for (int L = 1; L <= h->depth; ++L) {
         e = enqueue_levels(h, s, L);
@@ -636,6 +686,42 @@ ZMC_API int zmc_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c
     if (count < 0 || (count > 0 && !out)) return fail(nullptr, ZMC_ERR_ARG, "bad arguments");
     cudaError_t e = launch_philox(seed, c0, c1, c2, c3, count, out, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "philox launch");
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_set_profiling(zmc_handle h, int on) {
+    if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle");
+    if ((on != 0) != h->profiling) {
+        h->profiling = on != 0;
+        h->graph_stale = true;
+    }
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_profile(zmc_handle h, double* eval_ms, int* levels) {
+    if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle");
+    if (!h->profiling || !h->graph) return fail(h, ZMC_ERR_ARG, "profiling was not on for a run");
+    DeviceGuard g(h->device);
+    State st;
+    cudaError_t e = cudaMemcpy(&st, h->buf.state, sizeof st, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "state read-back");
+    int ran = 0;
+    for (int L = 1; L <= h->depth; ++L) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, h->ev[L][0], h->ev[L][1]);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventElapsedTime");
+        if (eval_ms) eval_ms[L - 1] = ms;
+        if (st.cells[L] > 0) ++ran;
+    }
+    if (levels) *levels = ran;
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_run_info(zmc_handle h, int64_t* kernels, int64_t* h2d_bytes, int64_t* d2h_bytes) {
+    if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle");
+    if (kernels) *kernels = h->graph_kernels;
+    if (h2d_bytes) *h2d_bytes = (int64_t)sizeof(Desc);
+    if (d2h_bytes) *d2h_bytes = (int64_t)sizeof(zmc_result);
     return ZMC_OK;
 }
 

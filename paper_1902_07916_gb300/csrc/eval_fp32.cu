@@ -1,8 +1,8 @@
-// FP32-evaluation instantiations of the sampling kernel (kernel (a)):
-// FP64 accumulation and FP32 Kahan accumulation.
+// FP32-evaluation / FP64-accumulation instantiations of the sampling kernel.
 #include "eval_kernel.cuh"
 
 namespace zmc {
-const void* eval_kernel_fp32_fp64acc(int fn) { return eval_kernel_for<ZMC_FP32_FP64ACC>(fn); }
-const void* eval_kernel_fp32_kahan(int fn) { return eval_kernel_for<ZMC_FP32_KAHAN>(fn); }
+const void* eval_kernel_fp32_fp64acc(int fn, bool wide) {
+    return eval_kernel_for<ZMC_FP32_FP64ACC>(fn, wide);
+}
 }  // namespace zmc

@@ -360,11 +360,25 @@ zmc_final(const State* __restrict__ st, const double* __restrict__ part_acc, int
 }
 
 // Philox words for bit-exact checks of the generator used by kernel (a).
-__global__ void zmc_philox_fill(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1,
-                                uint32_t c2, uint32_t c3, int64_t count, uint4* out) {
+// Same code path as the sampling kernel: (c1, c2, c3) play (t, q, L).
+__global__ void zmc_philox_fill(const PhiloxKeys keys, uint32_t c0, uint32_t c1, uint32_t c2,
+                                uint32_t c3, int64_t count, uint4* out) {
+    const StreamConst sc = stream_const(keys, c1, c2, c3);
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < count;
          b += (int64_t)gridDim.x * blockDim.x)
-        out[b] = philox4x32_10(make_uint4(c0 + (uint32_t)b, c1, c2, c3), k0, k1);
+        out[b] = philox_stream(keys, sc, c0 + (uint32_t)b);
+}
+
+PhiloxKeys philox_keys(uint64_t seed) {
+    PhiloxKeys K;
+    uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        K.k0[r] = k0;
+        K.k1[r] = k1;
+        k0 += kPhiloxWeylA;
+        k1 += kPhiloxWeylB;
+    }
+    return K;
 }
 
 // ------------------------------------------------------------- launchers
@@ -396,9 +410,8 @@ cudaError_t launch_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
     if (count <= 0) return cudaSuccess;
     int64_t blocks = (count + 255) / 256;
     if (blocks > 4096) blocks = 4096;
-    zmc_philox_fill<<<(int)blocks, 256, 0, s>>>((uint32_t)(seed & 0xFFFFFFFFu),
-                                               (uint32_t)(seed >> 32), c0, c1, c2, c3,
-                                               count, reinterpret_cast<uint4*>(out));
+    zmc_philox_fill<<<(int)blocks, 256, 0, s>>>(philox_keys(seed), c0, c1, c2, c3, count,
+                                               reinterpret_cast<uint4*>(out));
     return cudaGetLastError();
 }
 

@@ -17,16 +17,47 @@ constexpr uint32_t kPhiloxMulB = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxWeylA = 0x9E3779B9u;  // 2^32 * (golden ratio - 1)
 constexpr uint32_t kPhiloxWeylB = 0xBB67AE85u;  // 2^32 * (sqrt(3) - 1)
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+// Round keys of one seed: k0 + r * WeylA, k1 + r * WeylB for r = 0..9.
+// Computed once on the host and passed by value, so the kernels read them
+// as constant-bank operands of the XOR instructions.
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+};
+
+// Rounds 1 and 2 of every block of one (level L, slot q, trial t) stream
+// have parts that depend on (t, q, L) only: with counter (c0, t, q, L),
+// round 1 multiplies c0 and q, and round 2 multiplies round 1's first word,
+// which does not involve c0.  Those products are taken once per stream.
+struct StreamConst {
+    uint32_t r1z;  // L ^ k1[0]:                  round 1, word 2 = hi(A c0) ^ r1z
+    uint32_t r2x;  // lo(B q) ^ k0[1]:            round 2, word 0 = hi(B z1) ^ r2x
+    uint32_t r2z;  // hi(A x1) ^ k1[1]:           round 2, word 2 = r2z ^ lo(A c0)
+    uint32_t r2w;  // lo(A x1), x1 = hi(B q) ^ t ^ k0[0]: round 2, word 3
+};
+
+__device__ __forceinline__ StreamConst stream_const(const PhiloxKeys& K, uint32_t t,
+                                                    uint32_t q, uint32_t L) {
+    const uint32_t x1 = __umulhi(kPhiloxMulB, q) ^ t ^ K.k0[0];
+    StreamConst s;
+    s.r1z = L ^ K.k1[0];
+    s.r2x = (kPhiloxMulB * q) ^ K.k0[1];
+    s.r2z = __umulhi(kPhiloxMulA, x1) ^ K.k1[1];
+    s.r2w = kPhiloxMulA * x1;
+    return s;
+}
+
+// Philox4x32-10 of counter (c0, t, q, L) given the stream's constants.
+__device__ __forceinline__ uint4 philox_stream(const PhiloxKeys& K, const StreamConst& s,
+                                               uint32_t c0) {
+    const uint32_t hi0 = __umulhi(kPhiloxMulA, c0), lo0 = kPhiloxMulA * c0;   // round 1
+    const uint32_t z1 = hi0 ^ s.r1z;
+    const uint32_t hi1 = __umulhi(kPhiloxMulB, z1), lo1 = kPhiloxMulB * z1;   // round 2
+    uint4 c = make_uint4(hi1 ^ s.r2x, lo1, s.r2z ^ lo0, s.r2w);
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(kPhiloxMulA, c.x);
-        const uint32_t lo0 = kPhiloxMulA * c.x;
-        const uint32_t hi1 = __umulhi(kPhiloxMulB, c.z);
-        const uint32_t lo1 = kPhiloxMulB * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += kPhiloxWeylA;
-        k1 += kPhiloxWeylB;
+    for (int r = 2; r < 10; ++r) {
+        const uint32_t h0 = __umulhi(kPhiloxMulA, c.x), l0 = kPhiloxMulA * c.x;
+        const uint32_t h1 = __umulhi(kPhiloxMulB, c.z), l1 = kPhiloxMulB * c.z;
+        c = make_uint4(h1 ^ c.y ^ K.k0[r], l1, h0 ^ c.w ^ K.k1[r], l0);
     }
     return c;
 }
@@ -48,6 +79,52 @@ __device__ __forceinline__ float one_plus_word_f32(uint32_t w) {
     return __uint_as_float(0x3F800000u | (w >> 9));
 }
 
+// ------------------------------------------------ elementary functions
+// FP64 mode uses the CUDA math library.  FP32 mode reduces the argument of
+// sin/cos by 2 pi with a two-constant Cody-Waite step (Cody and Waite, 1980;
+// 2 pi split into a 13-bit head, so k * head is exact for |k| < 2^11, and a
+// tail) and evaluates the hardware sine/cosine on [-pi, pi] (absolute error
+// about 2^-21); exp goes through the hardware 2^x.  Arguments beyond the
+// reduction's range are reduced in FP64 instead (a rare, slower path).
+constexpr float kTwoPiHead = 0x1.922p+2f;        // 2 pi to 13 significant bits
+constexpr float kTwoPiTail = -0x1.2aeef4p-16f;   // 2 pi - head, to FP32
+constexpr float kInvTwoPi = 0x1.45f306p-3f;      // 1 / (2 pi), to FP32
+constexpr float kFastTrigLimit = 8192.0f;        // |k| <= 1304 < 2^11
+constexpr float kLog2E = 0x1.715476p+0f;         // log2(e), to FP32
+
+__device__ __forceinline__ float reduce_two_pi(float x) {
+    const float k = rintf(x * kInvTwoPi);
+    return fmaf(-k, kTwoPiTail, fmaf(-k, kTwoPiHead, x));
+}
+static __device__ __noinline__ float reduce_two_pi_wide(float x) {
+    const double xd = (double)x;
+    const double k = rint(xd * 0.15915494309189535);            // 1 / (2 pi)
+    return (float)fma(-k, 2.4492935982947064e-16, fma(-k, 6.283185307179586, xd));
+}
+// WIDE = false: the caller has proven |x| <= kFastTrigLimit.
+template <bool WIDE>
+__device__ __forceinline__ float zsin(float x) {
+    if constexpr (WIDE)
+        return __sinf(fabsf(x) <= kFastTrigLimit ? reduce_two_pi(x) : reduce_two_pi_wide(x));
+    else
+        return __sinf(reduce_two_pi(x));
+}
+template <bool WIDE>
+__device__ __forceinline__ float zcos(float x) {
+    if constexpr (WIDE)
+        return __cosf(fabsf(x) <= kFastTrigLimit ? reduce_two_pi(x) : reduce_two_pi_wide(x));
+    else
+        return __cosf(reduce_two_pi(x));
+}
+__device__ __forceinline__ float zexp(float x) { return exp2f(x * kLog2E); }
+__device__ __forceinline__ float zrcp(float x) { return __frcp_rn(x); }
+template <bool WIDE>
+__device__ __forceinline__ double zsin(double x) { return sin(x); }
+template <bool WIDE>
+__device__ __forceinline__ double zcos(double x) { return cos(x); }
+__device__ __forceinline__ double zexp(double x) { return exp(x); }
+__device__ __forceinline__ double zrcp(double x) { return 1.0 / x; }
+
 // ------------------------------------------------------------ integrands
 // Every registry integrand is a fold over the dimensions followed by a
 // finishing function: f(x) = finish(fold_i(acc, x_i, pa_i, pb_i)).  The
@@ -59,27 +136,27 @@ struct Fn;
 template <typename R> struct Fn<kConstant, R> {      // c0
     static __device__ __forceinline__ R init() { return R(0); }
     static __device__ __forceinline__ R fold(R a, R, R, R) { return a; }
-    static __device__ __forceinline__ R finish(R, const R* c, int) { return c[0]; }
+    template <bool W> static __device__ __forceinline__ R finish(R, const R* c, int) { return c[0]; }
 };
 template <typename R> struct Fn<kLinear, R> {        // c0 + sum pa_i x_i
     static __device__ __forceinline__ R init() { return R(0); }
     static __device__ __forceinline__ R fold(R a, R x, R pa, R) { return fma(pa, x, a); }
-    static __device__ __forceinline__ R finish(R a, const R* c, int) { return c[0] + a; }
+    template <bool W> static __device__ __forceinline__ R finish(R a, const R* c, int) { return c[0] + a; }
 };
 template <typename R> struct Fn<kSinSum, R> {        // sin(sum x_i), Eq. (1)
     static __device__ __forceinline__ R init() { return R(0); }
     static __device__ __forceinline__ R fold(R a, R x, R, R) { return a + x; }
-    static __device__ __forceinline__ R finish(R a, const R*, int) { return sin(a); }
+    template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int) { return zsin<W>(a); }
 };
 template <typename R> struct Fn<kGaussNorm, R> {     // c1 exp(c0 |x|^2), Eq. (2)
     static __device__ __forceinline__ R init() { return R(0); }
     static __device__ __forceinline__ R fold(R a, R x, R, R) { return fma(x, x, a); }
-    static __device__ __forceinline__ R finish(R a, const R* c, int) { return c[1] * exp(c[0] * a); }
+    template <bool W> static __device__ __forceinline__ R finish(R a, const R* c, int) { return c[1] * zexp(c[0] * a); }
 };
 template <typename R> struct Fn<kGenzOsc, R> {       // cos(c0 + sum pa_i x_i)
     static __device__ __forceinline__ R init() { return R(0); }
     static __device__ __forceinline__ R fold(R a, R x, R pa, R) { return fma(pa, x, a); }
-    static __device__ __forceinline__ R finish(R a, const R* c, int) { return cos(c[0] + a); }
+    template <bool W> static __device__ __forceinline__ R finish(R a, const R* c, int) { return zcos<W>(c[0] + a); }
 };
 template <typename R> struct Fn<kGenzProdPeak, R> {  // 1 / prod (pb_i + (x_i - pa_i)^2)
     static __device__ __forceinline__ R init() { return R(1); }
@@ -87,7 +164,7 @@ template <typename R> struct Fn<kGenzProdPeak, R> {  // 1 / prod (pb_i + (x_i - 
         const R t = x - pa;
         return a * fma(t, t, pb);
     }
-    static __device__ __forceinline__ R finish(R a, const R*, int) { return R(1) / a; }
+    template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int) { return zrcp(a); }
 };
 template <typename R> struct Fn<kGenzGauss, R> {     // exp(-sum (pa_i (x_i - pb_i))^2)
     static __device__ __forceinline__ R init() { return R(0); }
@@ -95,14 +172,14 @@ template <typename R> struct Fn<kGenzGauss, R> {     // exp(-sum (pa_i (x_i - pb
         const R t = pa * (x - pb);
         return fma(t, t, a);
     }
-    static __device__ __forceinline__ R finish(R a, const R*, int) { return exp(-a); }
+    template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int) { return zexp(-a); }
 };
 template <typename R> struct Fn<kGenzCorner, R> {    // (1 + sum pa_i x_i)^-(d+1)
     static __device__ __forceinline__ R init() { return R(1); }
     static __device__ __forceinline__ R fold(R a, R x, R pa, R) { return fma(pa, x, a); }
-    static __device__ __forceinline__ R finish(R a, const R*, int d) {
+    template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int d) {
         // r^(d+1) with r = 1/a, by binary powering
-        R r = R(1) / a, p = R(1);
+        R r = zrcp(a), p = R(1);
         for (int e = d + 1; e; e >>= 1) {
             if (e & 1) p *= r;
             r *= r;

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "zmc_layout.h"
+#include "zmc_device.cuh"
 
 namespace zmc {
 
@@ -42,6 +43,9 @@ cudaError_t launch_select(const Buffers& b, int level, const uint32_t* parents_p
                           uint32_t* parents_next, cudaStream_t s);
 // Kernel (c): compensated final reduction into the result.
 cudaError_t launch_final(const Buffers& b, cudaStream_t s);
+
+// Round keys of a seed (host side).
+PhiloxKeys philox_keys(uint64_t seed);
 
 cudaError_t launch_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
                           uint32_t c3, int64_t count, uint32_t* out,

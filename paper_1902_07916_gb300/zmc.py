@@ -105,6 +105,9 @@ def _load():
         "zmc_philox_words": [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                              ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
                              ctypes.c_void_p, ctypes.c_void_p],
+        "zmc_set_profiling": [H, ctypes.c_int],
+        "zmc_profile": [H, P(ctypes.c_double), P(ctypes.c_int)],
+        "zmc_run_info": [H, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)],
         "zmc_last_error": [H],
         "zmc_destroy": [H],
     }
@@ -232,6 +235,25 @@ def zmc_philox_words(seed, c0, c1, c2, c3, count, out_ptr, stream=None):
                                  c1 & 0xFFFFFFFF, c2 & 0xFFFFFFFF, c3 & 0xFFFFFFFF,
                                  int(count), ctypes.c_void_p(int(out_ptr)),
                                  _stream_ptr(stream)))
+
+
+def zmc_set_profiling(h, on: bool):
+    _check(_lib.zmc_set_profiling(h, 1 if on else 0), h)
+
+
+def zmc_profile(h, depth: int):
+    """(per-level sampling-kernel milliseconds, levels that had cells)."""
+    ms = (ctypes.c_double * max(1, depth))()
+    levels = ctypes.c_int()
+    _check(_lib.zmc_profile(h, ms, ctypes.byref(levels)), h)
+    return list(ms[:depth]), levels.value
+
+
+def zmc_run_info(h):
+    """(kernels per run, host->device bytes and device->host bytes per call)."""
+    k, i, o = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.zmc_run_info(h, ctypes.byref(k), ctypes.byref(i), ctypes.byref(o)), h)
+    return k.value, i.value, o.value
 
 
 def zmc_last_error(h=None) -> str:
