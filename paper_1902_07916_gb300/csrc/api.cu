@@ -226,7 +226,9 @@ int ensure_device(zmc_ctx* h) {
     const Req reqs[] = {
         {(void**)&b.desc, sizeof(Desc)},
         {(void**)&b.state, sizeof(State)},
-        {(void**)&b.sums, sizeof(double2) * (size_t)cap * h->T},
+        // partial sums of the sampling kernel's units: a level with `tiles`
+        // tiles has at most tiles + kTargetUnits units (see unit_chunks)
+        {(void**)&b.sums, sizeof(double2) * ((size_t)cap * h->T + (size_t)kTargetUnits)},
         {(void**)&b.cell_stats, sizeof(double2) * (size_t)cap},
         {(void**)&b.parents[0], sizeof(uint32_t) * (size_t)cap_par * h->dim},
         {(void**)&b.parents[1], sizeof(uint32_t) * (size_t)cap_par * h->dim},
@@ -463,7 +465,11 @@ int run_traced(zmc_ctx* h, cudaStream_t s) {
             tl.cell_stats.resize((size_t)tl.cells * 2);
             tl.parents_out.resize((size_t)tl.flagged * h->dim);
             const uint32_t* next = h->buf.parents[(L + 1) & 1];
-            e = cudaMemcpy(tl.sums.data(), h->buf.sums, tl.sums.size() * 8, cudaMemcpyDeviceToHost);
+            // the statistics kernel left each tile's total in its first unit slot
+            const int64_t chunks = unit_chunks(tl.cells * h->T, (h->n + 3) / 4);
+            e = cudaMemcpy2D(tl.sums.data(), sizeof(double2), h->buf.sums,
+                             sizeof(double2) * (size_t)chunks, sizeof(double2),
+                             (size_t)tl.cells * h->T, cudaMemcpyDeviceToHost);
             if (e == cudaSuccess)
                 e = cudaMemcpy(tl.cell_stats.data(), h->buf.cell_stats, tl.cell_stats.size() * 8,
                                cudaMemcpyDeviceToHost);

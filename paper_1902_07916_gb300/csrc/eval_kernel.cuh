@@ -1,31 +1,36 @@
 // Kernel (a): the fused sample-generate / evaluate / reduce kernel.
 //
-// One CTA owns one (cell, trial) tile at a time and walks the level's tiles
-// persistently (tile += gridDim.x); the number of cells of the level is read
-// from device memory, so the host never needs it.  Per tile:
-//   1. d threads decode the cell's lattice coordinates from the slot index
+// Work is cut into units: a unit is a contiguous range of the four-point
+// groups of one (cell, trial) tile (unit_chunks() units per tile).  Every warp
+// walks the level's units persistently and independently (unit += number of
+// warps in the grid); the level's cell count is read from device memory, so
+// the host never needs it.  Per unit:
+//   1. lanes < d decode the cell's lattice coordinates from the slot index
 //      (level 1: base-k digits; deeper: parent coordinates * k + child digit)
-//      into per-dimension (width, shift) pairs in shared memory;
-//   2. every thread takes groups of four consecutive samples; for each
+//      and fold the cell's geometry into the integrand's per-dimension
+//      coefficients, in the warp's slice of shared memory;
+//   2. every lane takes groups of four consecutive samples; for each
 //      dimension one Philox4x32-10 block (counter (g*d + i, t, q, L)) gives
 //      that dimension's coordinate for all four samples (Sec. 2.2: random
 //      numbers are produced where they are used, nothing is stored);
-//   3. the values f and f^2 are summed per thread, then across the warp with
-//      shuffles and across warps through shared memory, and one thread writes
-//      the tile's (S1, S2) as two doubles.
+//   3. f and f^2 are summed per lane, then across the warp with shuffles, and
+//      lane 0 writes the unit's (S1, S2) to the partial-sum array.  The
+//      statistics kernel adds a tile's units in a fixed order.
+// No CTA-wide barrier is involved, and the summation order depends on n, d
+// and the level's size only -- not on the CTA size or grid chosen to run it.
 //
 // The dimension loop is compiled for every d in 1..16 (a switch picks the
-// copy once per tile) and unrolled by four, so up to four Philox chains of
-// successive dimensions interleave with little loop control.  Registry
-// integrands fold each coordinate into four independent accumulators as it
-// is produced; expression integrands (compiled at run time) keep the four
-// points' coordinates in registers and evaluate the expression on each.
+// copy once per unit) and unrolled, so the Philox chains of successive
+// dimensions interleave.  Registry integrands fold each coordinate into four
+// independent accumulators as it is produced; expression integrands
+// (compiled at run time, d fixed) keep the four points' coordinates in
+// registers and evaluate the expression on each.
 //
 // MODE 0: FP64 throughout.  MODE 1: FP32 points and integrand, FP32 partial
-// sums over 16 groups (64 points) flushed into FP64 per-thread sums, FP64
-// block reduction.  MODE 2: FP32 points and integrand with TwoSum-compensated
-// per-thread sums and a TwoSum block reduction; the (sum, error) float pair
-// is widened to FP64 only for the stored result.
+// sums over 16 groups (64 points) flushed into FP64 per-lane sums, FP64 warp
+// reduction.  MODE 2: FP32 points and integrand with TwoSum-compensated
+// per-lane sums and a TwoSum warp reduction; the (sum, error) float pair is
+// widened to FP64 only for the stored result.
 #pragma once
 
 #include "zmc_device.cuh"
@@ -33,12 +38,13 @@
 namespace zmc {
 
 constexpr int kEvalMaxThreads = 256;
+constexpr int kEvalMaxWarps = kEvalMaxThreads / 32;
 // CTAs of kEvalMaxThreads per SM the register allocation must allow: caps
-// registers at 42 (FP32 modes) and 85 (FP64, whose values take two).
+// registers at 64 (FP32 modes) and 85 (FP64, whose values take two).
 template <int MODE>
-constexpr int eval_min_blocks() { return MODE == ZMC_FP64 ? 3 : 5; }
-// Philox chains of successive dimensions in flight per thread.
-constexpr int kDimUnroll = 4;
+constexpr int eval_min_blocks() { return MODE == ZMC_FP64 ? 3 : 4; }
+// Philox chains of successive dimensions in flight per lane.
+constexpr int kDimUnroll = 8;
 constexpr int kFlushGroups = 16;  // groups per FP32 partial sum (MODE 1)
 
 template <int MODE>
@@ -52,27 +58,24 @@ struct ModeTraits<ZMC_FP64> {
     using R2 = double2;
 };
 
+// The assembled 1.m value of a word in the mode's precision.
 template <int MODE>
-__device__ __forceinline__ typename ModeTraits<MODE>::R point(uint32_t w,
-                                                            typename ModeTraits<MODE>::R2 wb) {
-    if constexpr (MODE == ZMC_FP64) return fma(one_plus_word_f64(w), wb.x, wb.y);
-    else return fmaf(one_plus_word_f32(w), wb.x, wb.y);
+__device__ __forceinline__ typename ModeTraits<MODE>::R unit_point(uint32_t w) {
+    if constexpr (MODE == ZMC_FP64) return one_plus_word_f64(w);
+    else return one_plus_word_f32(w);
 }
 
-// Per-thread running sums of f and f^2 in the mode's arithmetic.  MODE 1
-// keeps its FP64 sums in shared memory (one double2 per thread, touched once
-// per 64 points) so they hold no registers in the sampling loop.
+// Per-lane running sums of f and f^2 in the mode's arithmetic.  MODE 1 keeps
+// its FP64 sums in the lane's shared-memory slot (touched once per 64
+// points), so they hold no registers in the sampling loop.
 template <int MODE>
-struct ThreadSums {
-    double S1d = 0.0, S2d = 0.0;                   // MODE 0 (MODE 1: at the end only)
+struct LaneSums {
     float s1 = 0.f, e1 = 0.f, s2 = 0.f, e2 = 0.f;  // MODE 1 partials / MODE 2 (sum, err)
-    double2* slot = nullptr;                       // MODE 1: this thread's FP64 sums
+    double S1d = 0.0, S2d = 0.0;                   // MODE 0
+    double2* slot;                                 // MODE 1
 
-    __device__ __forceinline__ explicit ThreadSums(double2* s_acc) {
-        if constexpr (MODE == ZMC_FP32_FP64ACC) {
-            slot = s_acc + threadIdx.x;
-            *slot = make_double2(0.0, 0.0);
-        }
+    __device__ __forceinline__ explicit LaneSums(double2* s) : slot(s) {
+        if constexpr (MODE == ZMC_FP32_FP64ACC) *slot = make_double2(0.0, 0.0);
     }
 
     template <typename R>
@@ -103,88 +106,36 @@ struct ThreadSums {
         }
     }
 
-    // Block reduction; thread 0 writes the tile's (S1, S2) and flags a
-    // non-finite result.  Ends with a barrier so shared memory can be reused.
-    __device__ __forceinline__ void reduce_store(double2* sums, int64_t tile, State* st) {
-        __shared__ double s_red[32][2];
-        __shared__ float s_redf[32][4];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const int nwarps = blockDim.x >> 5;
-        double a = 0.0, b = 0.0;
-        if constexpr (MODE != ZMC_FP32_KAHAN) {
-            if constexpr (MODE == ZMC_FP32_FP64ACC) {
-                const double2 v = *slot;
-                S1d = v.x;
-                S2d = v.y;
-            }
-            S1d = warp_sum(S1d);
-            S2d = warp_sum(S2d);
-            if (lane == 0) { s_red[warp][0] = S1d; s_red[warp][1] = S2d; }
-            __syncthreads();
-            if (warp == 0) {
-                a = warp_sum(lane < nwarps ? s_red[lane][0] : 0.0);
-                b = warp_sum(lane < nwarps ? s_red[lane][1] : 0.0);
-            }
+    // Warp reduction; lane 0 writes the unit's (S1, S2).
+    __device__ __forceinline__ void reduce_store(double2* out) {
+        double a, b;
+        if constexpr (MODE == ZMC_FP64) {
+            a = warp_sum(S1d);
+            b = warp_sum(S2d);
+        } else if constexpr (MODE == ZMC_FP32_FP64ACC) {
+            const double2 v = *slot;
+            a = warp_sum(v.x);
+            b = warp_sum(v.y);
         } else {
-            merge_pairs();
-            if (lane == 0) {
-                s_redf[warp][0] = s1; s_redf[warp][1] = e1;
-                s_redf[warp][2] = s2; s_redf[warp][3] = e2;
-            }
-            __syncthreads();
-            if (warp == 0) {
-                s1 = lane < nwarps ? s_redf[lane][0] : 0.f;
-                e1 = lane < nwarps ? s_redf[lane][1] : 0.f;
-                s2 = lane < nwarps ? s_redf[lane][2] : 0.f;
-                e2 = lane < nwarps ? s_redf[lane][3] : 0.f;
-                merge_pairs();
-                a = (double)s1 + (double)e1;
-                b = (double)s2 + (double)e2;
-            }
-        }
-        if (threadIdx.x == 0) {
-            sums[tile] = make_double2(a, b);
-            if (!(isfinite(a) && isfinite(b))) atomicMax(&st->status, ZMC_ERR_NONFINITE);
-        }
-        __syncthreads();
-    }
-
-    // Warp-wide TwoSum merge of the (sum, err) pairs: error terms are carried.
-    __device__ __forceinline__ void merge_pairs() {
 #pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const float os1 = __shfl_xor_sync(0xFFFFFFFFu, s1, o);
-            const float oe1 = __shfl_xor_sync(0xFFFFFFFFu, e1, o);
-            const float os2 = __shfl_xor_sync(0xFFFFFFFFu, s2, o);
-            const float oe2 = __shfl_xor_sync(0xFFFFFFFFu, e2, o);
-            float t, r;
-            two_sum(s1, os1, t, r); s1 = t; e1 = e1 + oe1 + r;
-            two_sum(s2, os2, t, r); s2 = t; e2 = e2 + oe2 + r;
+            for (int o = 16; o; o >>= 1) {
+                const float os1 = __shfl_xor_sync(0xFFFFFFFFu, s1, o);
+                const float oe1 = __shfl_xor_sync(0xFFFFFFFFu, e1, o);
+                const float os2 = __shfl_xor_sync(0xFFFFFFFFu, s2, o);
+                const float oe2 = __shfl_xor_sync(0xFFFFFFFFu, e2, o);
+                float t, r;
+                two_sum(s1, os1, t, r); s1 = t; e1 = e1 + oe1 + r;
+                two_sum(s2, os2, t, r); s2 = t; e2 = e2 + oe2 + r;
+            }
+            a = (double)s1 + (double)e1;
+            b = (double)s2 + (double)e2;
         }
+        if ((threadIdx.x & 31) == 0) *out = make_double2(a, b);
     }
 };
 
-// Per-tile set-up: the cell's per-dimension (width, shift) pairs.  The shift
-// turns the assembled 1.m value into the uniform (1 - 2^-33 in FP64,
-// 1 - 2^-24 in FP32), so that point = fma(1.m, w_L, shift) = lo + (c + u) w_L.
-template <int MODE>
-__device__ __forceinline__ void tile_setup(const Desc& D, int level, int64_t q,
-                                           const uint32_t* parents,
-                                           typename ModeTraits<MODE>::R2* s_wb) {
-    using R = typename ModeTraits<MODE>::R;
-    const double shift = (MODE == ZMC_FP64) ? 1.0 - 0x1p-33 : 1.0 - 0x1p-24;
-    const int tid = threadIdx.x;
-    if (tid < D.d) {
-        const double w = D.width[level][tid];
-        const int64_t c = cell_coord(D, level, q, tid, parents);
-        s_wb[tid].x = (R)w;
-        s_wb[tid].y = (R)(D.lo[tid] + (double)c * w - shift * w);
-    }
-    __syncthreads();
-}
-
-// Mask the points past n in the last group (only it can be short): `tail`
-// is the number of real points of the last group, 1..4.
+// Mask the points past n in the tile's last group (only it can be short):
+// `tail` is the number of real points of that group, 1..4.
 template <typename R>
 __device__ __forceinline__ void mask_tail(bool last, uint32_t tail, R& f1, R& f2, R& f3) {
     if (last) {
@@ -194,33 +145,110 @@ __device__ __forceinline__ void mask_tail(bool last, uint32_t tail, R& f1, R& f2
     }
 }
 
-// The sample loop of one tile for a registry integrand, dimension DIM.
+// Decomposition of the level's work into units (see unit_chunks()).
+struct UnitPlan {
+    int64_t units, chunks;
+    uint32_t ngroups, tail;
+    int T;
+};
+
+__device__ __forceinline__ UnitPlan unit_plan(const Desc& D, int64_t C) {
+    UnitPlan p;
+    p.T = D.T;
+    p.ngroups = (uint32_t)((D.n + 3) >> 2);                 // < 2^32: n * d < 2^34
+    p.tail = (uint32_t)(D.n - 4 * (int64_t)(p.ngroups - 1));
+    const int64_t tiles = C * D.T;
+    p.chunks = unit_chunks(tiles, p.ngroups);
+    p.units = tiles * p.chunks;
+    return p;
+}
+
+// Unit u -> (slot q, trial t, group range [g0, g1)).
+struct Unit {
+    int64_t q;
+    uint32_t t, g0, g1;
+};
+
+__device__ __forceinline__ Unit unit_of(const UnitPlan& p, int64_t u) {
+    Unit r;
+    const int64_t tile = u / p.chunks;
+    const int64_t chunk = u - tile * p.chunks;
+    r.q = tile / p.T;
+    r.t = (uint32_t)(tile - r.q * p.T);
+    r.g0 = (uint32_t)(chunk * p.ngroups / p.chunks);
+    r.g1 = (uint32_t)((chunk + 1) * p.ngroups / p.chunks);
+    return r;
+}
+
+// The cell's shift b_i = lo_i + c_i w_L - s w_L, where s turns the assembled
+// 1.m value into the uniform (1 - 2^-33 in FP64, 1 - 2^-24 in FP32), so that
+// the point is x_i = w_L * 1.m + b_i = lo_i + (c_i + u) w_L.
+template <int MODE>
+__device__ __forceinline__ double cell_shift(const Desc& D, int level, int64_t q, int i,
+                                             const uint32_t* parents, double w) {
+    const double s = (MODE == ZMC_FP64) ? 1.0 - 0x1p-33 : 1.0 - 0x1p-24;
+    const int64_t c = cell_coord(D, level, q, i, parents);
+    return D.lo[i] + (double)c * w - s * w;
+}
+
+// Per-unit set-up of a registry integrand (lanes < d, then a warp barrier):
+// each dimension's fold coefficients (alpha, beta) from the cell's width and
+// shift (see Fn), and the fold's start value init + sum_i term_i (FP64,
+// rounded once).
+template <int MODE, int FN>
+__device__ __forceinline__ typename ModeTraits<MODE>::R fold_setup(
+    const Desc& D, int level, int64_t q, const uint32_t* parents,
+    typename ModeTraits<MODE>::R2* w_coef, double* w_term) {
+    using R = typename ModeTraits<MODE>::R;
+    using F = Fn<FN, R>;
+    const int lane = threadIdx.x & 31;
+    if (lane < D.d) {
+        const double w = D.width[level][lane];
+        const double b = cell_shift<MODE>(D, level, q, lane, parents, w);
+        const Prep p = F::prep(w, b, D.pa[lane], D.pb[lane]);
+        w_coef[lane].x = (R)p.alpha;
+        w_coef[lane].y = (R)p.beta;
+        w_term[lane] = p.term;
+    }
+    __syncwarp();
+    double a0 = (double)F::init();
+    for (int i = 0; i < D.d; ++i) a0 += w_term[i];
+    return (R)a0;
+}
+
+// The sample loop of one unit for a registry integrand, dimension DIM.
+// Round 1's product A * c0 is carried as a 64-bit running sum: c0 = g*DIM+i
+// grows by one per dimension and by 32*DIM per group of this lane.
 template <int MODE, int FN, bool WIDE, int DIM>
-__device__ __forceinline__ void sample_tile_fold(
-    ThreadSums<MODE>& acc, const PhiloxKeys& keys, const StreamConst& sc,
-    const typename ModeTraits<MODE>::R2* s_wb, const typename ModeTraits<MODE>::R2* s_ab,
-    const typename ModeTraits<MODE>::R* s_c, uint32_t ngroups, uint32_t tail) {
+__device__ __forceinline__ void sample_unit_fold(
+    LaneSums<MODE>& acc, const PhiloxKeys& keys, const StreamConst& sc,
+    const typename ModeTraits<MODE>::R2* w_coef, const typename ModeTraits<MODE>::R* s_pb,
+    const typename ModeTraits<MODE>::R* s_c, typename ModeTraits<MODE>::R start,
+    uint32_t g0, uint32_t g1, uint32_t last_group, uint32_t tail) {
     using R = typename ModeTraits<MODE>::R;
     using R2 = typename ModeTraits<MODE>::R2;
     using F = Fn<FN, R>;
-    uint32_t g = threadIdx.x;
-    while (g < ngroups) {
-        for (int j = 0; j < kFlushGroups && g < ngroups; ++j, g += blockDim.x) {
-            R a0 = F::init(), a1 = F::init(), a2 = F::init(), a3 = F::init();
-            const uint32_t cbase = g * DIM;
+    const uint64_t step = (uint64_t)kPhiloxMulA * (uint64_t)(32 * DIM);
+    uint32_t g = g0 + (threadIdx.x & 31);
+    uint64_t Pg = (uint64_t)kPhiloxMulA * (uint64_t)(g * DIM);
+    while (g < g1) {
+        for (int j = 0; j < kFlushGroups && g < g1; ++j, g += 32, Pg += step) {
+            R a0 = start, a1 = start, a2 = start, a3 = start;
+            uint64_t P = Pg;
 #pragma unroll kDimUnroll
             for (int i = 0; i < DIM; ++i) {
-                const uint4 w = philox_stream(keys, sc, cbase + i);
-                const R2 wb = s_wb[i];
-                const R2 ab = s_ab[i];
-                a0 = F::fold(a0, point<MODE>(w.x, wb), ab.x, ab.y);
-                a1 = F::fold(a1, point<MODE>(w.y, wb), ab.x, ab.y);
-                a2 = F::fold(a2, point<MODE>(w.z, wb), ab.x, ab.y);
-                a3 = F::fold(a3, point<MODE>(w.w, wb), ab.x, ab.y);
+                const uint4 w = philox_from_product(keys, sc, (uint32_t)(P >> 32), (uint32_t)P);
+                P += kPhiloxMulA;
+                const R2 ab = w_coef[i];
+                const R pb = s_pb[i];
+                a0 = F::fold(a0, unit_point<MODE>(w.x), ab.x, ab.y, pb);
+                a1 = F::fold(a1, unit_point<MODE>(w.y), ab.x, ab.y, pb);
+                a2 = F::fold(a2, unit_point<MODE>(w.z), ab.x, ab.y, pb);
+                a3 = F::fold(a3, unit_point<MODE>(w.w), ab.x, ab.y, pb);
             }
             R f0 = F::template finish<WIDE>(a0, s_c, DIM), f1 = F::template finish<WIDE>(a1, s_c, DIM);
             R f2 = F::template finish<WIDE>(a2, s_c, DIM), f3 = F::template finish<WIDE>(a3, s_c, DIM);
-            mask_tail(g == ngroups - 1, tail, f1, f2, f3);
+            mask_tail(g == last_group, tail, f1, f2, f3);
             acc.add4(f0, f1, f2, f3);
         }
         acc.flush();
@@ -229,40 +257,37 @@ __device__ __forceinline__ void sample_tile_fold(
 
 template <int MODE, int FN, bool WIDE>
 __global__ void __launch_bounds__(kEvalMaxThreads, eval_min_blocks<MODE>())
-zmc_eval_reduce(const Desc* __restrict__ desc, State* __restrict__ st,
-                const uint32_t* __restrict__ parents, double2* __restrict__ sums,
+zmc_eval_reduce(const Desc* __restrict__ desc, const State* __restrict__ st,
+                const uint32_t* __restrict__ parents, double2* __restrict__ partial,
                 int level, const PhiloxKeys keys) {
     using R = typename ModeTraits<MODE>::R;
     using R2 = typename ModeTraits<MODE>::R2;
-    __shared__ R2 s_wb[ZMC_MAX_DIM], s_ab[ZMC_MAX_DIM];
-    __shared__ R s_c[4];
+    __shared__ R2 s_coef[kEvalMaxWarps][ZMC_MAX_DIM];
+    __shared__ double s_term[kEvalMaxWarps][ZMC_MAX_DIM];
+    __shared__ R s_pb[ZMC_MAX_DIM], s_c[4];
     __shared__ double2 s_acc[MODE == ZMC_FP32_FP64ACC ? kEvalMaxThreads : 1];
 
     const Desc& D = *desc;
     const int64_t C = st->cells[level];
     if (C <= 0) return;
-    const int d = D.d, T = D.T;
-    const int64_t n = D.n;
-    const int64_t tiles = C * T;
-    const uint32_t ngroups = (uint32_t)((n + 3) >> 2);        // < 2^32: n * d < 2^34
-    const uint32_t tail = (uint32_t)(n - 4 * (int64_t)(ngroups - 1));
-    const int tid = threadIdx.x;
-
-    if (tid < d) {
-        s_ab[tid].x = (R)D.pa[tid];
-        s_ab[tid].y = (R)D.pb[tid];
-    }
+    const int d = D.d;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid < d) s_pb[tid] = (R)D.pb[tid];
     if (tid < 4) s_c[tid] = (R)D.c[tid];
+    __syncthreads();
 
-    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int64_t q = tile / T;
-        const uint32_t t = (uint32_t)(tile - q * T);
-        tile_setup<MODE>(D, level, q, parents, s_wb);
-        const StreamConst sc = stream_const(keys, t, (uint32_t)q, (uint32_t)level);
-        ThreadSums<MODE> acc(s_acc);
-#define ZMC_FOLD_CASE(DD)                                                              \
-    case DD:                                                                           \
-        sample_tile_fold<MODE, FN, WIDE, DD>(acc, keys, sc, s_wb, s_ab, s_c, ngroups, tail); \
+    const UnitPlan plan = unit_plan(D, C);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double2* slot = &s_acc[MODE == ZMC_FP32_FP64ACC ? tid : 0];
+    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; u < plan.units; u += nwarps) {
+        const Unit un = unit_of(plan, u);
+        const R start = fold_setup<MODE, FN>(D, level, un.q, parents, s_coef[warp], s_term[warp]);
+        const StreamConst sc = stream_const(keys, un.t, (uint32_t)un.q, (uint32_t)level);
+        LaneSums<MODE> acc(slot);
+#define ZMC_FOLD_CASE(DD)                                                                      \
+    case DD:                                                                                   \
+        sample_unit_fold<MODE, FN, WIDE, DD>(acc, keys, sc, s_coef[warp], s_pb, s_c, start,    \
+                                             un.g0, un.g1, plan.ngroups - 1, plan.tail);       \
         break;
         switch (d) {
             ZMC_FOLD_CASE(1) ZMC_FOLD_CASE(2) ZMC_FOLD_CASE(3) ZMC_FOLD_CASE(4)
@@ -272,67 +297,73 @@ zmc_eval_reduce(const Desc* __restrict__ desc, State* __restrict__ st,
             default: break;
         }
 #undef ZMC_FOLD_CASE
-        acc.reduce_store(sums, tile, st);
+        acc.reduce_store(partial + u);
+        __syncwarp();   // the warp's coefficient slice is rewritten by the next unit
     }
 }
 
 // Body of the kernel for an expression integrand E with dimension DIM known
 // at compile time: E::eval(x, p) reads x[0..DIM-1] and the parameters p[].
 template <int MODE, int DIM, class E>
-__device__ __forceinline__ void eval_expr_body(const Desc* __restrict__ desc, State* __restrict__ st,
+__device__ __forceinline__ void eval_expr_body(const Desc* __restrict__ desc,
+                                               const State* __restrict__ st,
                                                const uint32_t* __restrict__ parents,
-                                               double2* __restrict__ sums, int level,
+                                               double2* __restrict__ partial, int level,
                                                const PhiloxKeys& keys) {
     using R = typename ModeTraits<MODE>::R;
     using R2 = typename ModeTraits<MODE>::R2;
-    __shared__ R2 s_wb[ZMC_MAX_DIM];
+    __shared__ R2 s_wb[kEvalMaxWarps][ZMC_MAX_DIM];
     __shared__ R s_p[2 * ZMC_MAX_DIM + 4];
     __shared__ double2 s_acc[MODE == ZMC_FP32_FP64ACC ? kEvalMaxThreads : 1];
 
     const Desc& D = *desc;
     const int64_t C = st->cells[level];
     if (C <= 0) return;
-    const int T = D.T;
-    const int64_t n = D.n;
-    const int64_t tiles = C * T;
-    const uint32_t ngroups = (uint32_t)((n + 3) >> 2);
-    const uint32_t tail = (uint32_t)(n - 4 * (int64_t)(ngroups - 1));
-    const int tid = threadIdx.x;
-
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid < ZMC_MAX_DIM) {
         s_p[tid] = (R)D.pa[tid];
         s_p[ZMC_MAX_DIM + tid] = (R)D.pb[tid];
     }
     if (tid < 4) s_p[2 * ZMC_MAX_DIM + tid] = (R)D.c[tid];
+    __syncthreads();
 
-    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int64_t q = tile / T;
-        const uint32_t t = (uint32_t)(tile - q * T);
-        tile_setup<MODE>(D, level, q, parents, s_wb);
-        const StreamConst sc = stream_const(keys, t, (uint32_t)q, (uint32_t)level);
-        ThreadSums<MODE> acc(s_acc);
-        uint32_t g = tid;
-        while (g < ngroups) {
-            for (int j = 0; j < kFlushGroups && g < ngroups; ++j, g += blockDim.x) {
+    const UnitPlan plan = unit_plan(D, C);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double2* slot = &s_acc[MODE == ZMC_FP32_FP64ACC ? tid : 0];
+    R2* wb = s_wb[warp];
+    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; u < plan.units; u += nwarps) {
+        const Unit un = unit_of(plan, u);
+        if (lane < DIM) {
+            const double w = D.width[level][lane];
+            wb[lane].x = (R)w;
+            wb[lane].y = (R)cell_shift<MODE>(D, level, un.q, lane, parents, w);
+        }
+        __syncwarp();
+        const StreamConst sc = stream_const(keys, un.t, (uint32_t)un.q, (uint32_t)level);
+        LaneSums<MODE> acc(slot);
+        uint32_t g = un.g0 + lane;
+        while (g < un.g1) {
+            for (int j = 0; j < kFlushGroups && g < un.g1; ++j, g += 32) {
                 R x0[DIM], x1[DIM], x2[DIM], x3[DIM];
                 const uint32_t cbase = g * DIM;
 #pragma unroll
                 for (int i = 0; i < DIM; ++i) {
                     const uint4 w = philox_stream(keys, sc, cbase + i);
-                    const R2 wb = s_wb[i];
-                    x0[i] = point<MODE>(w.x, wb);
-                    x1[i] = point<MODE>(w.y, wb);
-                    x2[i] = point<MODE>(w.z, wb);
-                    x3[i] = point<MODE>(w.w, wb);
+                    const R2 c = wb[i];
+                    x0[i] = fma(unit_point<MODE>(w.x), c.x, c.y);
+                    x1[i] = fma(unit_point<MODE>(w.y), c.x, c.y);
+                    x2[i] = fma(unit_point<MODE>(w.z), c.x, c.y);
+                    x3[i] = fma(unit_point<MODE>(w.w), c.x, c.y);
                 }
                 R f0 = E::eval(x0, s_p), f1 = E::eval(x1, s_p);
                 R f2 = E::eval(x2, s_p), f3 = E::eval(x3, s_p);
-                mask_tail(g == ngroups - 1, tail, f1, f2, f3);
+                mask_tail(g == plan.ngroups - 1, plan.tail, f1, f2, f3);
                 acc.add4(f0, f1, f2, f3);
             }
             acc.flush();
         }
-        acc.reduce_store(sums, tile, st);
+        acc.reduce_store(partial + u);
+        __syncwarp();
     }
 }
 

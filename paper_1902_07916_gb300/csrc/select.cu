@@ -136,7 +136,7 @@ __global__ void zmc_init_state(State* st, int64_t level1_cells) {
 // estimates I_{c,t} = V S1 / n; over the level the mean mu and population
 // standard deviation sigma of the spreads; theta = mu + m sigma.
 __global__ void __launch_bounds__(kSelThreads)
-zmc_cell_stats(const Desc* __restrict__ desc, State* st, const double2* __restrict__ sums,
+zmc_cell_stats(const Desc* __restrict__ desc, State* st, double2* __restrict__ sums,
                double2* __restrict__ cell_stats, double* part, int level) {
     const Desc& D = *desc;
     const int64_t C = st->cells[level];
@@ -147,21 +147,41 @@ zmc_cell_stats(const Desc* __restrict__ desc, State* st, const double2* __restri
     int64_t begin, end;
     chunk_of(C, begin, end);
 
+    // The sampling kernel left unit_chunks() partial sums per (cell, trial)
+    // tile, contiguous per tile; add them in order and keep the total in the
+    // tile's first slot.
+    const int64_t chunks = unit_chunks(C * T, (D.n + 3) >> 2);
+    bool finite = true;
     Moments acc{0.0, 0.0, 0.0};
     for (int64_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
-        const double2* row = sums + q * T;
+        double2* row = sums + q * T * chunks;
+        if (chunks > 1) {
+            for (int t = 0; t < T; ++t) {
+                double2 S = row[t * chunks];
+                for (int64_t c = 1; c < chunks; ++c) {
+                    S.x += row[t * chunks + c].x;
+                    S.y += row[t * chunks + c].y;
+                }
+                row[t * chunks] = S;
+            }
+        }
         double s = 0.0;
-        for (int t = 0; t < T; ++t) s += V * row[t].x / n;
+        for (int t = 0; t < T; ++t) {
+            const double2 S = row[t * chunks];
+            finite = finite && isfinite(S.x) && isfinite(S.y);
+            s += V * S.x / n;
+        }
         const double mean = s / T;
         double ss = 0.0;
         for (int t = 0; t < T; ++t) {
-            const double e = V * row[t].x / n - mean;
+            const double e = V * row[t * chunks].x / n - mean;
             ss += e * e;
         }
         const double spread = sqrt(ss / (T - 1));
         cell_stats[q] = make_double2(mean, spread);
         acc = merge(acc, Moments{1.0, spread, 0.0});
     }
+    if (!finite) atomicMax(&st->status, ZMC_ERR_NONFINITE);
     acc = block_merge(acc);
     if (threadIdx.x == 0) {
         part[3 * blockIdx.x + 0] = acc.n;

@@ -46,11 +46,13 @@ __device__ __forceinline__ StreamConst stream_const(const PhiloxKeys& K, uint32_
     return s;
 }
 
-// Philox4x32-10 of counter (c0, t, q, L) given the stream's constants.
-__device__ __forceinline__ uint4 philox_stream(const PhiloxKeys& K, const StreamConst& s,
-                                               uint32_t c0) {
-    const uint32_t hi0 = __umulhi(kPhiloxMulA, c0), lo0 = kPhiloxMulA * c0;   // round 1
-    const uint32_t z1 = hi0 ^ s.r1z;
+// Philox4x32-10 of counter (c0, t, q, L) given the stream's constants and
+// round 1's product A * c0 as (hi, lo).  The sampling kernel walks c0 in
+// steps of one, so it carries that product as a 64-bit running sum instead
+// of multiplying again.
+__device__ __forceinline__ uint4 philox_from_product(const PhiloxKeys& K, const StreamConst& s,
+                                                     uint32_t hi0, uint32_t lo0) {
+    const uint32_t z1 = hi0 ^ s.r1z;                                          // round 1
     const uint32_t hi1 = __umulhi(kPhiloxMulB, z1), lo1 = kPhiloxMulB * z1;   // round 2
     uint4 c = make_uint4(hi1 ^ s.r2x, lo1, s.r2z ^ lo0, s.r2w);
 #pragma unroll
@@ -62,19 +64,25 @@ __device__ __forceinline__ uint4 philox_stream(const PhiloxKeys& K, const Stream
     return c;
 }
 
+// Philox4x32-10 of counter (c0, t, q, L) given the stream's constants.
+__device__ __forceinline__ uint4 philox_stream(const PhiloxKeys& K, const StreamConst& s,
+                                               uint32_t c0) {
+    return philox_from_product(K, s, __umulhi(kPhiloxMulA, c0), kPhiloxMulA * c0);
+}
+
 // ------------------------------------------------------ word -> point maps
 // The stream of (level L, slot q, trial t): dimension i of samples 4g..4g+3
 // is the block with counter (g*d + i, t, q, L), one lane per sample.
 //
 // FP64 reading: u = (w + 1/2) 2^-32.  The double 1 + w 2^-32 is assembled
-// from the word's bits; x = lo + (c + u) w_L is then one FMA against the
-// per-cell shift base = lo + c w_L - (1 - 2^-33) w_L.
+// from the word's bits, and the point lo + (c + u) w_L is formed from it as
+// w_L * (1 + w 2^-32) + (lo + c w_L - (1 - 2^-33) w_L).
 __device__ __forceinline__ double one_plus_word_f64(uint32_t w) {
     return __hiloint2double(0x3FF00000 | (int)(w >> 12), (int)(w << 20));
 }
 // FP32 reading: u = (floor(w / 2^9) + 1/2) 2^-23, exact in binary32; the
-// float 1 + floor(w/2^9) 2^-23 is assembled from the bits, and
-// x = fma(1.m, w_L, base) with base = lo + c w_L - (1 - 2^-24) w_L.
+// float 1 + floor(w / 2^9) 2^-23 is assembled from the bits, and the point
+// is w_L * (1.m) + (lo + c w_L - (1 - 2^-24) w_L).
 __device__ __forceinline__ float one_plus_word_f32(uint32_t w) {
     return __uint_as_float(0x3F800000u | (w >> 9));
 }
@@ -127,56 +135,91 @@ __device__ __forceinline__ double zrcp(double x) { return 1.0 / x; }
 
 // ------------------------------------------------------------ integrands
 // Every registry integrand is a fold over the dimensions followed by a
-// finishing function: f(x) = finish(fold_i(acc, x_i, pa_i, pb_i)).  The
-// per-dimension pair (pa_i, pb_i) and scalars c[0..3] are laid out on the
-// host (api.cu) from the user's parameters.
+// finishing function.  The sampling kernel never forms the point itself: a
+// coordinate is x_i = w_i v + b_i with v = 1.m in [1, 2) assembled from the
+// Philox word, and each integrand folds the affine map into per-tile,
+// per-dimension constants computed in FP64 by prep():
+//   alpha_i, beta_i  -- the fold's coefficients of v,
+//   term_i           -- summed into the fold's start value,
+// so that fold(acc, v, alpha_i, beta_i, pb_i) costs one or two FMAs.  The
+// parameters (pa_i, pb_i, c[0..3]) are laid out by the host from the user's
+// list (api.cu).
 template <int FN, typename R>
 struct Fn;
 
+struct Prep {
+    double alpha, beta, term;
+};
+
 template <typename R> struct Fn<kConstant, R> {      // c0
+    static __device__ __forceinline__ Prep prep(double, double, double, double) { return {0, 0, 0}; }
     static __device__ __forceinline__ R init() { return R(0); }
-    static __device__ __forceinline__ R fold(R a, R, R, R) { return a; }
+    static __device__ __forceinline__ R fold(R a, R, R, R, R) { return a; }
     template <bool W> static __device__ __forceinline__ R finish(R, const R* c, int) { return c[0]; }
 };
 template <typename R> struct Fn<kLinear, R> {        // c0 + sum pa_i x_i
+    static __device__ __forceinline__ Prep prep(double w, double b, double pa, double) {
+        return {pa * w, 0.0, pa * b};
+    }
     static __device__ __forceinline__ R init() { return R(0); }
-    static __device__ __forceinline__ R fold(R a, R x, R pa, R) { return fma(pa, x, a); }
+    static __device__ __forceinline__ R fold(R a, R v, R al, R, R) { return fma(al, v, a); }
     template <bool W> static __device__ __forceinline__ R finish(R a, const R* c, int) { return c[0] + a; }
 };
 template <typename R> struct Fn<kSinSum, R> {        // sin(sum x_i), Eq. (1)
+    static __device__ __forceinline__ Prep prep(double w, double b, double, double) {
+        return {w, 0.0, b};
+    }
     static __device__ __forceinline__ R init() { return R(0); }
-    static __device__ __forceinline__ R fold(R a, R x, R, R) { return a + x; }
+    static __device__ __forceinline__ R fold(R a, R v, R al, R, R) { return fma(al, v, a); }
     template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int) { return zsin<W>(a); }
 };
 template <typename R> struct Fn<kGaussNorm, R> {     // c1 exp(c0 |x|^2), Eq. (2)
+    static __device__ __forceinline__ Prep prep(double w, double b, double, double) {
+        return {w, b, 0.0};
+    }
     static __device__ __forceinline__ R init() { return R(0); }
-    static __device__ __forceinline__ R fold(R a, R x, R, R) { return fma(x, x, a); }
+    static __device__ __forceinline__ R fold(R a, R v, R al, R be, R) {
+        const R x = fma(v, al, be);
+        return fma(x, x, a);
+    }
     template <bool W> static __device__ __forceinline__ R finish(R a, const R* c, int) { return c[1] * zexp(c[0] * a); }
 };
 template <typename R> struct Fn<kGenzOsc, R> {       // cos(c0 + sum pa_i x_i)
+    static __device__ __forceinline__ Prep prep(double w, double b, double pa, double) {
+        return {pa * w, 0.0, pa * b};
+    }
     static __device__ __forceinline__ R init() { return R(0); }
-    static __device__ __forceinline__ R fold(R a, R x, R pa, R) { return fma(pa, x, a); }
+    static __device__ __forceinline__ R fold(R a, R v, R al, R, R) { return fma(al, v, a); }
     template <bool W> static __device__ __forceinline__ R finish(R a, const R* c, int) { return zcos<W>(c[0] + a); }
 };
 template <typename R> struct Fn<kGenzProdPeak, R> {  // 1 / prod (pb_i + (x_i - pa_i)^2)
+    static __device__ __forceinline__ Prep prep(double w, double b, double pa, double) {
+        return {w, b - pa, 0.0};
+    }
     static __device__ __forceinline__ R init() { return R(1); }
-    static __device__ __forceinline__ R fold(R a, R x, R pa, R pb) {
-        const R t = x - pa;
+    static __device__ __forceinline__ R fold(R a, R v, R al, R be, R pb) {
+        const R t = fma(v, al, be);
         return a * fma(t, t, pb);
     }
     template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int) { return zrcp(a); }
 };
 template <typename R> struct Fn<kGenzGauss, R> {     // exp(-sum (pa_i (x_i - pb_i))^2)
+    static __device__ __forceinline__ Prep prep(double w, double b, double pa, double pb) {
+        return {pa * w, pa * (b - pb), 0.0};
+    }
     static __device__ __forceinline__ R init() { return R(0); }
-    static __device__ __forceinline__ R fold(R a, R x, R pa, R pb) {
-        const R t = pa * (x - pb);
+    static __device__ __forceinline__ R fold(R a, R v, R al, R be, R) {
+        const R t = fma(v, al, be);
         return fma(t, t, a);
     }
     template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int) { return zexp(-a); }
 };
 template <typename R> struct Fn<kGenzCorner, R> {    // (1 + sum pa_i x_i)^-(d+1)
+    static __device__ __forceinline__ Prep prep(double w, double b, double pa, double) {
+        return {pa * w, 0.0, pa * b};
+    }
     static __device__ __forceinline__ R init() { return R(1); }
-    static __device__ __forceinline__ R fold(R a, R x, R pa, R) { return fma(pa, x, a); }
+    static __device__ __forceinline__ R fold(R a, R v, R al, R, R) { return fma(al, v, a); }
     template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int d) {
         // r^(d+1) with r = 1/a, by binary powering
         R r = zrcp(a), p = R(1);

@@ -62,4 +62,23 @@ struct State {
     uint32_t ticket[4];  // last-block arrival counters (self-resetting)
 };
 
+// Work units of the sampling kernel.  A (cell, trial) tile is cut into
+// `chunks` units of about equal numbers of four-point groups so that a level
+// has at least kTargetUnits units when it can, but no unit has fewer than
+// kMinUnitGroups groups.  The count depends only on the level's tile count
+// and on n, never on the GPU, so neither do the results.
+constexpr int64_t kTargetUnits = int64_t(1) << 18;
+constexpr int64_t kMinUnitGroups = 1024;
+
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int64_t unit_chunks(int64_t tiles, int64_t ngroups) {
+    if (tiles <= 0) return 1;
+    int64_t want = (kTargetUnits + tiles - 1) / tiles;
+    int64_t most = ngroups / kMinUnitGroups;
+    if (most < 1) most = 1;
+    return want < most ? (want < 1 ? 1 : want) : most;
+}
+
 }  // namespace zmc
