@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "jit.h"
@@ -18,7 +19,6 @@ namespace zmc {
 const void* eval_kernel_fp64(int fn, bool wide);
 const void* eval_kernel_fp32_fp64acc(int fn, bool wide);
 const void* eval_kernel_fp32_kahan(int fn, bool wide);
-cudaError_t launch_batch(int count, zmc_handle const* hs, cudaStream_t s);
 }  // namespace zmc
 
 using namespace zmc;
@@ -443,6 +443,67 @@ int finish_result(zmc_ctx* h, zmc_result* out) {
     return out->status;
 }
 
+// Device tables and per-level graphs of the last batch, reused while the
+// same handles (same buffers, precision and depth) come back.
+struct BatchCache {
+    int device = -1, capacity = 0;
+    int count = 0, mode = -1, depth = 0;
+    std::vector<Buffers> sel;
+    std::vector<BatchEval> eval;
+    Desc* d_desc = nullptr;
+    Desc* h_desc = nullptr;            // pinned
+    Buffers* d_sel = nullptr;
+    BatchEval* d_eval = nullptr;
+    int64_t* d_l1 = nullptr;
+    int64_t* d_offsets = nullptr;
+    unsigned long long* d_head = nullptr;
+    zmc_result* d_out = nullptr;
+    zmc_result* h_out = nullptr;       // pinned
+    cudaStream_t cap = nullptr;
+    std::vector<cudaGraphExec_t> graphs;
+
+    void drop_graphs() {
+        for (cudaGraphExec_t g : graphs) cudaGraphExecDestroy(g);
+        graphs.clear();
+        count = 0;
+    }
+    void release() {
+        drop_graphs();
+        void* dev_ptrs[] = {d_desc, d_sel, d_eval, d_l1, d_offsets, d_head, d_out};
+        for (void* p : dev_ptrs)
+            if (p) cudaFree(p);
+        if (h_desc) cudaFreeHost(h_desc);
+        if (h_out) cudaFreeHost(h_out);
+        if (cap) cudaStreamDestroy(cap);
+        *this = BatchCache{};
+    }
+    int reserve(int n, int dev) {
+        if (dev == device && n <= capacity) return ZMC_OK;
+        release();
+        if (fault_injected("alloc")) return fail(nullptr, ZMC_ERR_OOM, "injected allocation failure");
+        cudaError_t e = cudaMalloc(&d_desc, sizeof(Desc) * n);
+        if (e == cudaSuccess) e = cudaMallocHost(&h_desc, sizeof(Desc) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&d_sel, sizeof(Buffers) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&d_eval, sizeof(BatchEval) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&d_l1, sizeof(int64_t) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&d_offsets, sizeof(int64_t) * (n + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&d_head, sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(zmc_result) * n);
+        if (e == cudaSuccess) e = cudaMallocHost(&h_out, sizeof(zmc_result) * n);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            release();
+            return cuda_fail(nullptr, e, "batch tables");
+        }
+        device = dev;
+        capacity = n;
+        return ZMC_OK;
+    }
+};
+
+std::mutex g_batch_mu;
+BatchCache g_batch;
+
 int run_traced(zmc_ctx* h, cudaStream_t s) {
     h->trace_levels.clear();
     plan_shapes(h);
@@ -679,10 +740,116 @@ ZMC_API int zmc_integrate_batch(int count, const zmc_handle* hs, void* stream,
                                 zmc_result* outs) {
     if (count < 0 || (count > 0 && (!hs || !outs)))
         return fail(nullptr, ZMC_ERR_ARG, "bad batch arguments");
+    if (count == 0) return ZMC_OK;
+    if (count > 65535) return fail(nullptr, ZMC_ERR_ARG, "at most 65535 integrals per batch");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+    const int mode = hs[0] ? hs[0]->mode : -1;
+    int depth = 0;
+    for (int i = 0; i < count; ++i) {
+        zmc_ctx* h = hs[i];
+        if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle in batch");
+        if (h->integrand < 0) return fail(nullptr, ZMC_ERR_NOINTEGRAND, "an integral has no integrand");
+        if (h->integrand >= kNumIntegrands)
+            return fail(nullptr, ZMC_ERR_ARG, "batched integrals need registry integrands");
+        if (h->mode != mode) return fail(nullptr, ZMC_ERR_ARG, "all integrals need the same precision");
+        if (h->device >= 0 && h->device != dev)
+            return fail(nullptr, ZMC_ERR_ARG, "all integrals must live on the current device");
+        depth = std::max(depth, h->depth);
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    BatchCache& B = g_batch;
+    for (int i = 0; i < count; ++i) {
+        int rc = ensure_device(hs[i]);
+        if (rc != ZMC_OK) {
+            g_error = hs[i]->last_error;
+            return rc;
+        }
+    }
+    int rc = B.reserve(count, dev);
+    if (rc != ZMC_OK) return rc;
+    // what the kernels are told about each integral
+    std::vector<Buffers> sel(count);
+    std::vector<BatchEval> ev(count);
+    std::vector<int64_t> l1(count);
+    for (int i = 0; i < count; ++i) {
+        zmc_ctx* h = hs[i];
+        sel[i] = h->buf;
+        sel[i].desc = B.d_desc + i;
+        ev[i].desc = B.d_desc + i;
+        ev[i].st = h->buf.state;
+        ev[i].sums = h->buf.sums;
+        ev[i].parents[0] = h->buf.parents[0];
+        ev[i].parents[1] = h->buf.parents[1];
+        ev[i].keys = philox_keys(h->seed);
+        ev[i].fn = h->integrand;
+        ev[i].wide = trig_argument_bound(h) > 0.99 * 8192.0 ? 1 : 0;
+        l1[i] = ipow_sat(h->k, h->dim, INT64_MAX);
+        build_desc(h, B.h_desc[i]);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool same = B.count == count && B.mode == mode && B.depth == depth &&
+                      !B.graphs.empty() &&
+                      memcmp(B.sel.data(), sel.data(), sizeof(Buffers) * count) == 0 &&
+                      memcmp(B.eval.data(), ev.data(), sizeof(BatchEval) * count) == 0;
+    if (!same) {
+        B.drop_graphs();
+        e = cudaMemcpy(B.d_sel, sel.data(), sizeof(Buffers) * count, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(B.d_eval, ev.data(), sizeof(BatchEval) * count, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(B.d_l1, l1.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch tables upload");
+        B.sel = sel;
+        B.eval = ev;
+        B.count = count;
+        B.mode = mode;
+        B.depth = depth;
+        int per_sm = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_eval_kernel(mode),
+                                                      kBatchThreads, 0);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int grid = std::max(1, per_sm) * std::max(1, sms);
+        for (int L = 1; L <= depth; ++L) {
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(B.cap, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch capture");
+            cudaError_t le = cudaSuccess;
+            if (L == 1) le = launch_init_batch(B.d_sel, B.d_l1, count, B.cap);
+            if (le == cudaSuccess)
+                le = launch_batch_level(B.d_eval, count, L, B.d_offsets, B.d_head, mode, grid, B.cap);
+            if (le == cudaSuccess) le = launch_select_batch(B.d_sel, count, L, B.cap);
+            if (le == cudaSuccess && L == depth) le = launch_final_batch(B.d_sel, B.d_out, count, B.cap);
+            e = cudaStreamEndCapture(B.cap, &g);
+            if (le != cudaSuccess || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                B.drop_graphs();
+                return cuda_fail(nullptr, le != cudaSuccess ? le : e, "batch level capture");
+            }
+            cudaGraphExec_t x = nullptr;
+            e = cudaGraphInstantiate(&x, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                B.drop_graphs();
+                return cuda_fail(nullptr, e, "batch graph instantiate");
+            }
+            B.graphs.push_back(x);
+        }
+    }
+    // the integrals' parameters, every call; then every level; then results
+    e = cudaMemcpyAsync(B.d_desc, B.h_desc, sizeof(Desc) * count, cudaMemcpyHostToDevice, s);
+    for (size_t L = 0; e == cudaSuccess && L < B.graphs.size(); ++L) e = cudaGraphLaunch(B.graphs[L], s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B.h_out, B.d_out, sizeof(zmc_result) * count, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch run");
     int first = ZMC_OK;
     for (int i = 0; i < count; ++i) {
-        int rc = zmc_integrate(hs[i], stream, &outs[i]);
-        if (rc != ZMC_OK && first == ZMC_OK) first = rc;
+        outs[i] = B.h_out[i];
+        // keep the handles' own descriptors in step for later single runs
+        hs[i]->desc_dirty = true;
+        if (outs[i].status != ZMC_OK && first == ZMC_OK) first = outs[i].status;
     }
     return first;
 }

@@ -216,27 +216,29 @@ __device__ __forceinline__ typename ModeTraits<MODE>::R fold_setup(
     return (R)a0;
 }
 
-// The sample loop of one unit for a registry integrand, dimension DIM.
-// Round 1's product A * c0 is carried as a 64-bit running sum: c0 = g*DIM+i
-// grows by one per dimension and by 32*DIM per group of this lane.
+// The sample loop of one unit for a registry integrand, dimension DIM (a
+// compile-time constant, or 0 to take the dimension from dim_rt).
+// Round 1's product A * c0 is carried as a 64-bit running sum: c0 = g*d+i
+// grows by one per dimension and by 32*d per group of this lane.
 template <int MODE, int FN, bool WIDE, int DIM>
 __device__ __forceinline__ void sample_unit_fold(
     LaneSums<MODE>& acc, const PhiloxKeys& keys, const StreamConst& sc,
     const typename ModeTraits<MODE>::R2* w_coef, const typename ModeTraits<MODE>::R* s_pb,
     const typename ModeTraits<MODE>::R* s_c, typename ModeTraits<MODE>::R start,
-    uint32_t g0, uint32_t g1, uint32_t last_group, uint32_t tail) {
+    uint32_t g0, uint32_t g1, uint32_t last_group, uint32_t tail, int dim_rt = 0) {
     using R = typename ModeTraits<MODE>::R;
     using R2 = typename ModeTraits<MODE>::R2;
     using F = Fn<FN, R>;
-    const uint64_t step = (uint64_t)kPhiloxMulA * (uint64_t)(32 * DIM);
+    const int nd = DIM > 0 ? DIM : dim_rt;
+    const uint64_t step = (uint64_t)kPhiloxMulA * (uint64_t)(32 * nd);
     uint32_t g = g0 + (threadIdx.x & 31);
-    uint64_t Pg = (uint64_t)kPhiloxMulA * (uint64_t)(g * DIM);
+    uint64_t Pg = (uint64_t)kPhiloxMulA * (uint64_t)(g * nd);
     while (g < g1) {
         for (int j = 0; j < kFlushGroups && g < g1; ++j, g += 32, Pg += step) {
             R a0 = start, a1 = start, a2 = start, a3 = start;
             uint64_t P = Pg;
 #pragma unroll kDimUnroll
-            for (int i = 0; i < DIM; ++i) {
+            for (int i = 0; i < nd; ++i) {
                 const uint4 w = philox_from_product(keys, sc, (uint32_t)(P >> 32), (uint32_t)P);
                 P += kPhiloxMulA;
                 const R2 ab = w_coef[i];
@@ -246,8 +248,8 @@ __device__ __forceinline__ void sample_unit_fold(
                 a2 = F::fold(a2, unit_point<MODE>(w.z), ab.x, ab.y, pb);
                 a3 = F::fold(a3, unit_point<MODE>(w.w), ab.x, ab.y, pb);
             }
-            R f0 = F::template finish<WIDE>(a0, s_c, DIM), f1 = F::template finish<WIDE>(a1, s_c, DIM);
-            R f2 = F::template finish<WIDE>(a2, s_c, DIM), f3 = F::template finish<WIDE>(a3, s_c, DIM);
+            R f0 = F::template finish<WIDE>(a0, s_c, nd), f1 = F::template finish<WIDE>(a1, s_c, nd);
+            R f2 = F::template finish<WIDE>(a2, s_c, nd), f3 = F::template finish<WIDE>(a3, s_c, nd);
             mask_tail(g == last_group, tail, f1, f2, f3);
             acc.add4(f0, f1, f2, f3);
         }

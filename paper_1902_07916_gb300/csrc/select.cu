@@ -124,8 +124,11 @@ __device__ bool last_to_arrive(uint32_t* ticket) {
 
 }  // namespace
 
+// Each step below is a device body run by one grid (or, for a batch of
+// integrals, by row blockIdx.y of a 2-D grid) and a thin kernel around it.
+
 // Reset the tree state of a run: level 1 is the full lattice.
-__global__ void zmc_init_state(State* st, int64_t level1_cells) {
+__device__ __forceinline__ void init_state_body(State* st, int64_t level1_cells) {
     uint32_t* w = reinterpret_cast<uint32_t*>(st);
     for (size_t i = threadIdx.x; i < sizeof(State) / 4; i += blockDim.x) w[i] = 0u;
     __syncthreads();
@@ -135,9 +138,10 @@ __global__ void zmc_init_state(State* st, int64_t level1_cells) {
 // Step (b1): per cell the mean and sample spread (ddof 1) of the trial
 // estimates I_{c,t} = V S1 / n; over the level the mean mu and population
 // standard deviation sigma of the spreads; theta = mu + m sigma.
-__global__ void __launch_bounds__(kSelThreads)
-zmc_cell_stats(const Desc* __restrict__ desc, State* st, double2* __restrict__ sums,
-               double2* __restrict__ cell_stats, double* part, int level) {
+__device__ __forceinline__ void cell_stats_body(const Desc* __restrict__ desc, State* st,
+                                                double2* __restrict__ sums,
+                                                double2* __restrict__ cell_stats, double* part,
+                                                int level) {
     const Desc& D = *desc;
     const int64_t C = st->cells[level];
     if (C <= 0) return;
@@ -208,9 +212,10 @@ zmc_cell_stats(const Desc* __restrict__ desc, State* st, double2* __restrict__ s
 // Step (b2): flag cells whose spread is strictly larger than theta (never at
 // the last level), count them per CTA, and let the last CTA scan the counts,
 // apply the refinement budget and publish the next level's size.
-__global__ void __launch_bounds__(kSelThreads)
-zmc_flag_count(const Desc* __restrict__ desc, State* st, const double2* __restrict__ cell_stats,
-               int64_t* part_count, int64_t* part_offset, double* part_margin, int level) {
+__device__ __forceinline__ void flag_count_body(const Desc* __restrict__ desc, State* st,
+                                                const double2* __restrict__ cell_stats,
+                                                int64_t* part_count, int64_t* part_offset,
+                                                double* part_margin, int level) {
     const Desc& D = *desc;
     const int64_t C = st->cells[level];
     if (C <= 0) return;
@@ -289,11 +294,13 @@ zmc_flag_count(const Desc* __restrict__ desc, State* st, const double2* __restri
 // the next level's parent list (the children themselves are implicit:
 // child slot r*K + digit); add the accepted cells' mean and spread^2 / T to
 // this level's compensated partial sums.
-__global__ void __launch_bounds__(kSelThreads)
-zmc_compact(const Desc* __restrict__ desc, const State* __restrict__ st,
-            const double2* __restrict__ cell_stats, const int64_t* __restrict__ part_offset,
-            const uint32_t* __restrict__ parents_prev, uint32_t* __restrict__ parents_next,
-            double* __restrict__ part_acc, int level) {
+__device__ __forceinline__ void compact_body(const Desc* __restrict__ desc,
+                                             const State* __restrict__ st,
+                                             const double2* __restrict__ cell_stats,
+                                             const int64_t* __restrict__ part_offset,
+                                             const uint32_t* __restrict__ parents_prev,
+                                             uint32_t* __restrict__ parents_next,
+                                             double* __restrict__ part_acc, int level) {
     const Desc& D = *desc;
     const int64_t C = st->cells[level];
     if (C <= 0) return;
@@ -344,9 +351,9 @@ zmc_compact(const Desc* __restrict__ desc, const State* __restrict__ st,
 
 // Step (c): the compensated sum of every level's accepted partial sums, and
 // the result record.  One CTA.
-__global__ void __launch_bounds__(kSelThreads)
-zmc_final(const State* __restrict__ st, const double* __restrict__ part_acc, int sel_grid,
-          zmc_result* __restrict__ out) {
+__device__ __forceinline__ void final_body(const State* __restrict__ st,
+                                           const double* __restrict__ part_acc, int sel_grid,
+                                           zmc_result* __restrict__ out) {
     const int levels = st->levels_run;
     CSum val{0.0, 0.0}, var{0.0, 0.0};
     for (int L = 1; L <= levels; ++L) {
@@ -377,6 +384,60 @@ zmc_final(const State* __restrict__ st, const double* __restrict__ part_acc, int
         out->levels_run = levels;
         out->status = st->status;
     }
+}
+
+// ---------------------------------------------------------------- kernels
+// One integration: the buffers are kernel arguments.
+__global__ void zmc_init_state(State* st, int64_t level1_cells) {
+    init_state_body(st, level1_cells);
+}
+__global__ void __launch_bounds__(kSelThreads)
+zmc_cell_stats(const Desc* desc, State* st, double2* sums, double2* cell_stats, double* part,
+               int level) {
+    cell_stats_body(desc, st, sums, cell_stats, part, level);
+}
+__global__ void __launch_bounds__(kSelThreads)
+zmc_flag_count(const Desc* desc, State* st, const double2* cell_stats, int64_t* part_count,
+               int64_t* part_offset, double* part_margin, int level) {
+    flag_count_body(desc, st, cell_stats, part_count, part_offset, part_margin, level);
+}
+__global__ void __launch_bounds__(kSelThreads)
+zmc_compact(const Desc* desc, const State* st, const double2* cell_stats,
+            const int64_t* part_offset, const uint32_t* parents_prev, uint32_t* parents_next,
+            double* part_acc, int level) {
+    compact_body(desc, st, cell_stats, part_offset, parents_prev, parents_next, part_acc, level);
+}
+__global__ void __launch_bounds__(kSelThreads)
+zmc_final(const State* st, const double* part_acc, int sel_grid, zmc_result* out) {
+    final_body(st, part_acc, sel_grid, out);
+}
+
+// A batch of integrations: row blockIdx.y of the grid works on items[y].
+// Level L reads the parent list written by level L-1 (ping-pong by parity).
+__global__ void zmc_init_state_batch(const Buffers* items, const int64_t* level1_cells) {
+    init_state_body(items[blockIdx.y].state, level1_cells[blockIdx.y]);
+}
+__global__ void __launch_bounds__(kSelThreads)
+zmc_cell_stats_batch(const Buffers* items, int level) {
+    const Buffers& b = items[blockIdx.y];
+    cell_stats_body(b.desc, b.state, b.sums, b.cell_stats, b.part_stats, level);
+}
+__global__ void __launch_bounds__(kSelThreads)
+zmc_flag_count_batch(const Buffers* items, int level) {
+    const Buffers& b = items[blockIdx.y];
+    flag_count_body(b.desc, b.state, b.cell_stats, b.part_count, b.part_offset, b.part_margin,
+                    level);
+}
+__global__ void __launch_bounds__(kSelThreads)
+zmc_compact_batch(const Buffers* items, int level) {
+    const Buffers& b = items[blockIdx.y];
+    compact_body(b.desc, b.state, b.cell_stats, b.part_offset, b.parents[level & 1],
+                 b.parents[(level + 1) & 1], b.part_acc, level);
+}
+__global__ void __launch_bounds__(kSelThreads)
+zmc_final_batch(const Buffers* items, zmc_result* out) {
+    const Buffers& b = items[blockIdx.y];
+    final_body(b.state, b.part_acc, kSelGrid, &out[blockIdx.y]);
 }
 
 // Philox words for bit-exact checks of the generator used by kernel (a).
@@ -422,6 +483,25 @@ cudaError_t launch_select(const Buffers& b, int level, const uint32_t* parents_p
 
 cudaError_t launch_final(const Buffers& b, cudaStream_t s) {
     zmc_final<<<1, kSelThreads, 0, s>>>(b.state, b.part_acc, kSelGrid, b.result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_batch(const Buffers* items, const int64_t* level1_cells, int count,
+                              cudaStream_t s) {
+    zmc_init_state_batch<<<dim3(1, count), 256, 0, s>>>(items, level1_cells);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_batch(const Buffers* items, int count, int level, cudaStream_t s) {
+    const dim3 grid(kSelGrid, count);
+    zmc_cell_stats_batch<<<grid, kSelThreads, 0, s>>>(items, level);
+    zmc_flag_count_batch<<<grid, kSelThreads, 0, s>>>(items, level);
+    zmc_compact_batch<<<grid, kSelThreads, 0, s>>>(items, level);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final_batch(const Buffers* items, zmc_result* out, int count, cudaStream_t s) {
+    zmc_final_batch<<<dim3(1, count), kSelThreads, 0, s>>>(items, out);
     return cudaGetLastError();
 }
 

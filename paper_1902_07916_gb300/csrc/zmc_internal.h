@@ -47,6 +47,30 @@ cudaError_t launch_final(const Buffers& b, cudaStream_t s);
 // Round keys of a seed (host side).
 PhiloxKeys philox_keys(uint64_t seed);
 
+// CTA size of the batched sampling kernel.
+constexpr int kBatchThreads = 256;
+
+// What the batched sampling kernel needs of one integral.
+struct BatchEval {
+    const Desc* desc;
+    const State* st;
+    double2* sums;
+    const uint32_t* parents[2];
+    PhiloxKeys keys;
+    int32_t fn, wide;
+};
+
+// Batched form (batch.cu, select.cu): `items` / `level1_cells` / `out` are
+// device arrays of `count` entries; row y of each selection grid works on
+// integral y.
+const void* batch_eval_kernel(int mode);
+cudaError_t launch_batch_level(const BatchEval* items, int count, int level, int64_t* offsets,
+                               unsigned long long* head, int mode, int grid, cudaStream_t s);
+cudaError_t launch_init_batch(const Buffers* items, const int64_t* level1_cells, int count,
+                              cudaStream_t s);
+cudaError_t launch_select_batch(const Buffers* items, int count, int level, cudaStream_t s);
+cudaError_t launch_final_batch(const Buffers* items, zmc_result* out, int count, cudaStream_t s);
+
 cudaError_t launch_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
                           uint32_t c3, int64_t count, uint32_t* out,
                           cudaStream_t s);
