@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--depth", type=int, default=None, help="override depth (profiling only)")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched leg")
     return p.parse_args()
 
 
@@ -262,6 +263,10 @@ def run_ours(args, world, rank, local):
                 "levels_run": r64.levels_run, "flagged_per_level": r64.flagged_per_level}
     it.close()
 
+    batched = None
+    if rank == 0 and not args.no_batch:
+        batched = run_batched(zmc, stream, prec)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, target_s=12.0)
@@ -303,9 +308,51 @@ def run_ours(args, world, rank, local):
                 "d2h_bytes_per_step": d2h_bytes},
         "gpu_launches": kernels_per_run * args.steps,
         "fp64": fp64,
+        "batched": batched,
         "cpu_baseline": cpu,
     }
     return line
+
+
+# ----------------------------------------------------------- batched leg
+
+BATCH_MAX_SAMPLES = 1 << 32     # per integral: about 2x the largest level 1
+
+
+def run_batched(zmc, stream, prec, steps: int = 3):
+    """512 Genz integrals (d 2..9, k 2..6, n 2^10..2^15, depth 1..4, 8 trials,
+    m = 2) through zmc_integrate_batch: one persistent sampling kernel per
+    level.  Timed end to end per call (parameters up, results down)."""
+    import torch
+    from paper_1902_07916_gb300 import workloads
+    ws = workloads.genz_batch(512, seed=0)
+    hs = []
+    try:
+        for w in ws:
+            h = zmc.zmc_create(w.dim, w.lo, w.hi, w.k, w.n, w.trials, w.depth,
+                               w.sigma_multiplier, w.seed)
+            hs.append(h)
+            zmc.zmc_set_integrand(h, w.integrand, w.params)
+            zmc.zmc_set_precision(h, prec)
+            zmc.zmc_set_limits(h, 1 << 24, max(BATCH_MAX_SAMPLES, w.level1_samples()))
+        zmc.zmc_integrate_batch(hs, stream)                 # warm-up: buffers, graphs
+        times, res = [], None
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = zmc.zmc_integrate_batch(hs, stream)
+            times.append(time.perf_counter() - t0)
+        samples = sum(r.samples for r in res)
+        return {"value": round(samples / (sum(times) / len(times)) / 1e9, 3), "unit": UNIT,
+                "integrals": len(ws), "samples_per_call": samples,
+                "ms_per_call": round(1e3 * sum(times) / len(times), 2), "steps": steps,
+                "budget": "2^32 points per integral (or its level 1)",
+                "budget_stopped": sum(1 for r in res if r.status == zmc.ZMC_ERR_BUDGET),
+                "timing": "host wall clock around zmc_integrate_batch (uploads, all levels, "
+                          "result download)"}
+    finally:
+        for h in hs:
+            zmc.zmc_destroy(h)
 
 
 # ------------------------------------------------------ CPU baseline
