@@ -231,6 +231,40 @@ ZMC_API int zmc_profile(zmc_handle h, double* eval_ms, int* levels);
 ZMC_API int zmc_run_info(zmc_handle h, int64_t* kernels, int64_t* h2d_bytes,
                          int64_t* d2h_bytes);
 
+/*
+ * zmc_level_stats_noalloc -- one tree level's per-cell statistics and
+ * threshold (the same arithmetic as the library's own selection step: trial
+ * estimates I = volume * S1 / n, per-cell mean and sample spread, and
+ * theta = mu + sigma_multiplier * sigma over the cells' spreads) for
+ * per-(cell, trial) sums the caller already holds, without allocating any
+ * device memory.  The paper has no counterpart; this exists for callers
+ * that cannot allocate device memory: applications whose device memory is
+ * all owned by their own pool or arena (a framework's caching allocator, a
+ * fixed budget carved out at start-up) and that forbid any other allocator,
+ * and latency-critical loops that cannot afford the device-wide
+ * synchronisation cudaMalloc and cudaFree may imply.
+ *   sums         device, cells * trials * 2 doubles: (S1, S2) per (cell,
+ *                trial), cell-major (the layout zmc_trace_level returns)
+ *   cells        1 .. 1048576 (the bound set by the entry point's scratch)
+ *   trials       >= 2;  n >= 1 points per (cell, trial)
+ *   volume       the cells' volume;  sigma_multiplier finite, >= 0
+ *   cell_stats   device, cells * 2 doubles out: (mean, spread) per cell
+ *   level_stats  device, 3 doubles out: (mu, sigma, theta)
+ * All outputs are written asynchronously on `stream`.  Scratch: a fixed
+ * static device array of about 24 KiB that every GPU using the library holds
+ * until the process exits, shared by all calls and keeping the last call's
+ * contents (each call clears what must start at zero).  Calls that overlap
+ * on the GPU (on different streams, or from different host threads) race on
+ * it and must be serialised by the caller.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.
+ * Errors: ZMC_ERR_ARG (sizes beyond the bound, NULL pointers, bad values;
+ * nothing is launched), ZMC_ERR_CUDA.
+ */
+ZMC_API int zmc_level_stats_noalloc(const double* sums, int64_t cells, int trials, int64_t n,
+                                    double volume, double sigma_multiplier, double* cell_stats,
+                                    double* level_stats, void* stream);
+
 /* zmc_last_error -- message of the last failed call on h (or of the last
  * failed zmc_create / handle-less call when h is NULL).  Never NULL; valid
  * until the next call on the same handle. */

@@ -898,6 +898,15 @@ ZMC_API int zmc_run_info(zmc_handle h, int64_t* kernels, int64_t* h2d_bytes, int
     return ZMC_OK;
 }
 
+ZMC_API int zmc_level_stats_noalloc(const double* sums, int64_t cells, int trials, int64_t n,
+                                    double volume, double sigma_multiplier, double* cell_stats,
+                                    double* level_stats, void* stream) {
+    const int rc = level_stats_noalloc(sums, cells, trials, n, volume, sigma_multiplier,
+                                       cell_stats, level_stats, (cudaStream_t)stream);
+    if (rc != ZMC_OK) return fail(nullptr, rc, noalloc_last_error());
+    return ZMC_OK;
+}
+
 ZMC_API const char* zmc_last_error(zmc_handle h) {
     return h ? h->last_error.c_str() : g_error.c_str();
 }

@@ -8,6 +8,10 @@
 #include <float.h>
 #include <math.h>
 
+#include <map>
+#include <mutex>
+#include <string>
+
 #include "zmc_device.cuh"
 #include "zmc_internal.h"
 
@@ -503,6 +507,134 @@ cudaError_t launch_select_batch(const Buffers* items, int count, int level, cuda
 cudaError_t launch_final_batch(const Buffers* items, zmc_result* out, int count, cudaStream_t s) {
     zmc_final_batch<<<dim3(1, count), kSelThreads, 0, s>>>(items, out);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------ no-allocation variant
+// zmc_level_stats_noalloc: the per-cell statistics and level threshold of
+// zmc_cell_stats for per-(cell, trial) sums the caller already holds, with
+// all scratch in the static array below instead of library-allocated
+// buffers.  One CTA per kNoAllocCellsPerBlock cells, so the array bounds the
+// number of cells a call accepts.
+constexpr int kNoAllocCellsPerBlock = 1024;
+constexpr int kNoAllocMaxBlocks = 1024;
+constexpr int64_t kNoAllocMaxCells = (int64_t)kNoAllocCellsPerBlock * kNoAllocMaxBlocks;
+
+// Per-CTA (count, mean, M2) partials, then the arrival ticket.  24 KiB +
+// 256 B, held by every GPU that loads the library until the process exits.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxBlocks * 3 + 32];
+
+__global__ void __launch_bounds__(kSelThreads)
+zmc_level_stats_noalloc_kernel(const double2* __restrict__ sums, int64_t C, int T, double n,
+                               double V, double m, double2* __restrict__ cell_stats,
+                               double* __restrict__ level_stats, double* scratch) {
+    double* part = scratch;
+    uint32_t* ticket = reinterpret_cast<uint32_t*>(scratch + kNoAllocMaxBlocks * 3);
+    int64_t begin, end;
+    chunk_of(C, begin, end);
+    Moments acc{0.0, 0.0, 0.0};
+    for (int64_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
+        const double2* row = sums + q * T;
+        double s = 0.0;
+        for (int t = 0; t < T; ++t) s += V * row[t].x / n;
+        const double mean = s / T;
+        double ss = 0.0;
+        for (int t = 0; t < T; ++t) {
+            const double e = V * row[t].x / n - mean;
+            ss += e * e;
+        }
+        const double spread = sqrt(ss / (T - 1));
+        cell_stats[q] = make_double2(mean, spread);
+        acc = merge(acc, Moments{1.0, spread, 0.0});
+    }
+    acc = block_merge(acc);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x + 0] = acc.n;
+        part[3 * blockIdx.x + 1] = acc.mean;
+        part[3 * blockIdx.x + 2] = acc.m2;
+    }
+    if (!last_to_arrive(ticket)) return;
+    Moments all{0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        all = merge(all, Moments{__ldcg(part + 3 * b), __ldcg(part + 3 * b + 1),
+                                 __ldcg(part + 3 * b + 2)});
+    all = block_merge(all);
+    if (threadIdx.x == 0) {
+        const double sigma = sqrt(all.m2 / all.n);
+        level_stats[0] = all.mean;
+        level_stats[1] = sigma;
+        level_stats[2] = all.mean + m * sigma;
+        *ticket = 0u;
+    }
+}
+
+namespace {
+std::mutex g_noalloc_mu;
+std::map<int, double*> g_noalloc_addr;   // device -> device address of the scratch
+
+// Once per device, with that device current: the device address of the
+// scratch array (in host code its name is only a host-side stand-in).
+int noalloc_scratch(int dev, double** out, std::string* why) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    auto it = g_noalloc_addr.find(dev);
+    if (it != g_noalloc_addr.end()) {
+        *out = it->second;
+        return ZMC_OK;
+    }
+    double* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        *why = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        return ZMC_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+    *out = p;
+    return ZMC_OK;
+}
+
+thread_local std::string g_noalloc_error;
+}  // namespace
+
+const char* noalloc_last_error() { return g_noalloc_error.c_str(); }
+
+int level_stats_noalloc(const double* sums, int64_t cells, int trials, int64_t n, double volume,
+                        double sigma_multiplier, double* cell_stats, double* level_stats,
+                        cudaStream_t s) {
+    if (!sums || !cell_stats || !level_stats) {
+        g_noalloc_error = "sums, cell_stats and level_stats must be device pointers";
+        return ZMC_ERR_ARG;
+    }
+    if (cells < 1 || cells > kNoAllocMaxCells) {
+        g_noalloc_error = "cells must be in 1.." + std::to_string(kNoAllocMaxCells) +
+                          " (the size of the static scratch of this entry point)";
+        return ZMC_ERR_ARG;
+    }
+    if (trials < 2 || n < 1 || !isfinite(volume) || !isfinite(sigma_multiplier) ||
+        sigma_multiplier < 0.0) {
+        g_noalloc_error = "need trials >= 2, n >= 1, finite volume, finite sigma_multiplier >= 0";
+        return ZMC_ERR_ARG;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        g_noalloc_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return ZMC_ERR_CUDA;
+    }
+    double* scratch = nullptr;
+    if (int rc = noalloc_scratch(dev, &scratch, &g_noalloc_error)) return rc;
+    // The scratch keeps the previous call's contents: the ticket must start at 0.
+    e = cudaMemsetAsync(scratch + kNoAllocMaxBlocks * 3, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) {
+        const int grid = (int)((cells + kNoAllocCellsPerBlock - 1) / kNoAllocCellsPerBlock);
+        zmc_level_stats_noalloc_kernel<<<grid, kSelThreads, 0, s>>>(
+            reinterpret_cast<const double2*>(sums), cells, trials, (double)n, volume,
+            sigma_multiplier, reinterpret_cast<double2*>(cell_stats), level_stats, scratch);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        g_noalloc_error = std::string("launch: ") + cudaGetErrorString(e);
+        return ZMC_ERR_CUDA;
+    }
+    return ZMC_OK;
 }
 
 cudaError_t launch_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,

@@ -47,6 +47,13 @@ cudaError_t launch_final(const Buffers& b, cudaStream_t s);
 // Round keys of a seed (host side).
 PhiloxKeys philox_keys(uint64_t seed);
 
+// zmc_level_stats_noalloc (select.cu): returns ZMC_OK or an error code with
+// the message in noalloc_last_error().
+int level_stats_noalloc(const double* sums, int64_t cells, int trials, int64_t n, double volume,
+                        double sigma_multiplier, double* cell_stats, double* level_stats,
+                        cudaStream_t s);
+const char* noalloc_last_error();
+
 // CTA size of the batched sampling kernel.
 constexpr int kBatchThreads = 256;
 

@@ -108,6 +108,9 @@ def _load():
         "zmc_set_profiling": [H, ctypes.c_int],
         "zmc_profile": [H, P(ctypes.c_double), P(ctypes.c_int)],
         "zmc_run_info": [H, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)],
+        "zmc_level_stats_noalloc": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p],
         "zmc_last_error": [H],
         "zmc_destroy": [H],
     }
@@ -254,6 +257,15 @@ def zmc_run_info(h):
     k, i, o = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(_lib.zmc_run_info(h, ctypes.byref(k), ctypes.byref(i), ctypes.byref(o)), h)
     return k.value, i.value, o.value
+
+
+def zmc_level_stats_noalloc(sums_ptr, cells, trials, n, volume, sigma_multiplier,
+                            cell_stats_ptr, level_stats_ptr, stream=None):
+    """Device pointers in, device pointers out; allocates nothing."""
+    _check(_lib.zmc_level_stats_noalloc(
+        ctypes.c_void_p(int(sums_ptr)), int(cells), int(trials), int(n), float(volume),
+        float(sigma_multiplier), ctypes.c_void_p(int(cell_stats_ptr)),
+        ctypes.c_void_p(int(level_stats_ptr)), _stream_ptr(stream)))
 
 
 def zmc_last_error(h=None) -> str:
