@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     p.add_argument("--no-batch", action="store_true", help="skip the batched leg")
+    p.add_argument("--paper", action="store_true",
+                   help="run the paper's parameter sets (Sec. 3) instead of the benchmark")
     return p.parse_args()
 
 
@@ -430,9 +432,66 @@ def run_reference(args, world, rank):
     }
 
 
+# ------------------------------------------------------ paper parameter sets
+
+def paper_runs():
+    """The paper's own parameter sets (Sec. 3), one GB300: (name, table,
+    workload).  Points per cell follow each version: n2^D for the TensorFlow
+    and multiprocessing runs, a flat count for the Ray runs."""
+    from paper_1902_07916_gb300.workloads import Workload
+    f1 = lambda name, k, n, T, depth, m: Workload(name, "sin_sum", 6, [0.0] * 6, [10.0] * 6,
+                                                  k, n, T, depth, m, 0)
+    f2 = lambda name, d, k, n, T, depth, m: Workload(name, "gauss_norm", d, [-1.0] * d,
+                                                     [1.0] * d, k, n, T, depth, m, 0, [0.01])
+    return [
+        ("f1 TF", "Tab. 1", f1("E1_tf", 3, 20 ** 6, 5, 2, 5.0)),
+        ("f1 Numba-MP", "Tab. 1", f1("E1_mp", 6, 10 ** 6, 5, 2, 5.0)),
+        ("f2 9-D Numba-MP", "Tab. 2", f2("E2_mp", 9, 3, 3 ** 9, 5, 4, 5.0)),
+        ("f1 Ray", "Tab. 3", f1("E3_ray", 12, 10 ** 4, 5, 1, 5.0)),
+        ("f2 9-D Ray", "Tab. 4", f2("E4_ray9", 9, 3, 10 ** 4, 5, 4, 4.0)),
+        ("f2 12-D Ray", "Tab. 4", f2("E4_ray12", 12, 3, 10 ** 4, 5, 4, 4.0)),
+    ]
+
+
+def run_paper(args):
+    """Each of the paper's parameter sets once (after a warm-up), FP64 and
+    FP32-mixed, timed end to end through zmc_integrate; results with the
+    closed forms, as context rows beside the paper's tables."""
+    import torch
+    from paper_1902_07916_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1902_07916_gb300 import zmc
+    from oracle import closed_forms
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for label, table, w in paper_runs():
+        exact = closed_forms.integral(w.integrand, w.lo, w.hi, w.params)
+        for prec in ("fp64", "fp32_fp64acc"):
+            with zmc.Integrator(w.dim, w.lo, w.hi, w.k, w.n, w.trials, w.depth,
+                                w.sigma_multiplier, w.seed, w.integrand, w.params,
+                                precision=zmc.PRECISIONS[prec]) as it:
+                it.integrate(stream)
+                t0 = time.perf_counter()
+                r = it.integrate(stream)
+                dt = time.perf_counter() - t0
+            rows.append({"run": label, "paper_table": table, "precision": prec,
+                         "cells_per_dim": w.k, "points_per_cell": w.n, "trials": w.trials,
+                         "depth": w.depth, "sigma_multiplier": w.sigma_multiplier,
+                         "result": r.value, "std": r.std, "closed_form": exact,
+                         "seconds": round(dt, 4), "samples": r.samples,
+                         "gsamples_per_s": round(r.samples / dt / 1e9, 2),
+                         "levels_run": r.levels_run, "flagged_per_level": r.flagged_per_level,
+                         "status": r.status})
+    return {"paper_parameter_sets": rows, "gpu": torch.cuda.get_device_name(0)}
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
+    if args.paper:
+        print(json.dumps(run_paper(args)), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
