@@ -96,6 +96,15 @@ def allreduce_sum(world, value):
     return float(t.item())
 
 
+def weak_scaling_value(world, local_ms, local_samples):
+    """Whole-job throughput: every rank integrated its own problem, so the
+    job's points are the sum over ranks and its time the slowest rank's.
+    Returns (max ms over ranks, total points, Gsamples/s)."""
+    t_max = allreduce_max(world, local_ms)
+    total = allreduce_sum(world, local_samples)
+    return t_max, total, total / (t_max * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -217,9 +226,7 @@ def run_ours(args, world, rank, local):
     clk = clocks.summary()
 
     total_ms = sum(step_ms)
-    t_max = allreduce_max(world, total_ms)
-    all_samples = allreduce_sum(world, float(sum(samples)))
-    value = all_samples / (t_max * 1e-3) / 1e9
+    t_max, all_samples, value = weak_scaling_value(world, total_ms, float(sum(samples)))
 
     # roofline of the dominant kernel (the sampling kernel)
     ops = sum(samples) * philox_multiplies_per_sample(w.dim)
