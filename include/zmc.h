@@ -61,9 +61,16 @@ extern "C" {
 /* ------------------------------------------------------- precision modes */
 #define ZMC_FP64 0             /* FP64 uniforms, points, integrand and sums */
 #define ZMC_FP32_FP64ACC 1     /* FP32 evaluation, FP32 partial sums over
-                                  64 points, FP64 per-thread and block sums */
+                                  80 points, FP64 per-thread and warp sums  */
 #define ZMC_FP32_KAHAN 2       /* FP32 evaluation, FP32 Kahan / two-sum
                                   accumulation up to the per-cell result     */
+/* The FP32 modes draw their points from the FP32 stream (five 23-bit
+ * uniforms per Philox block, see zmc_uniforms), so they sample other points
+ * than the FP64 mode does: their results differ from it by Monte Carlo
+ * noise as well as by rounding.  FP32 flushes integrand values below about
+ * 1e-38, so an integrand whose values on the coarse levels are all that
+ * small (a Gaussian of width 0.01 in 9-D seen from cells of width 2/3) gives
+ * the selection nothing to see: use ZMC_FP64 for it. */
 
 #define ZMC_MAX_DIM 16
 #define ZMC_MAX_DEPTH 16
@@ -213,6 +220,24 @@ ZMC_API int zmc_trace_level(zmc_handle h, int level, int64_t* cells,
 ZMC_API int zmc_philox_words(uint64_t seed, uint32_t c0, uint32_t c1,
                              uint32_t c2, uint32_t c3, int64_t count,
                              uint32_t* out, void* stream);
+
+/*
+ * zmc_uniforms -- the uniforms the sampling kernel draws, for bit-exact
+ * checks of the stream definition (Sec. 2.2: numbers produced where they are
+ * used; the generator and layout are this library's choice).  For points
+ * [first, first + count) of the stream of (level, slot, trial) under `seed`,
+ * writes u into out[(s - first) * dim + i] for every dimension i.
+ *   mode ZMC_FP64: dimension i of points 4g..4g+3 are the four 32-bit words
+ *     of the Philox4x32-10 block with counter (g*dim + i, trial, slot, level),
+ *     u = (w + 1/2) 2^-32;
+ *   mode ZMC_FP32_*: dimension i of points 5g..5g+4 are the five 23-bit
+ *     fields of that block read as a 128-bit integer (bits 23f .. 23f+22),
+ *     u = (field + 1/2) 2^-23.
+ * out: device pointer to count*dim doubles.  Asynchronous on `stream`.
+ * Errors: ZMC_ERR_ARG, ZMC_ERR_CUDA.
+ */
+ZMC_API int zmc_uniforms(uint64_t seed, int level, uint32_t slot, uint32_t trial, int dim,
+                         int mode, int64_t first, int64_t count, double* out, void* stream);
 
 /*
  * Instrumentation for measurement.

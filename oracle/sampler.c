@@ -19,13 +19,16 @@
  * as Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
  * easy as 1, 2, 3", SC'11) with
  *     key     = (seed mod 2^32, seed div 2^32)
- *     counter = ((s div 4) * d + i,  t,  q,  L)
- *     word    = output lane (s mod 4)
+ *     counter = ((s div G) * d + i,  t,  q,  L)
  * for sample s in [0, n), dimension i in [0, d), trial t, work-list slot q and
- * level L (1-based).  One Philox block thus carries dimension i of four
- * consecutive samples.
- *
- * Uniform: u = (w + 1/2) * 2^-32, exact in FP64 and strictly inside (0, 1).
+ * level L (1-based).  One Philox block thus carries dimension i of G
+ * consecutive samples:
+ *   FP64 stream (G = 4): sample s reads 32-bit word (s mod 4), and
+ *                        u = (w + 1/2) * 2^-32, exact in FP64;
+ *   FP32 stream (G = 5): sample s reads 23-bit field (s mod 5) of the block
+ *                        read as a 128-bit integer (bits 23 f .. 23 f + 22),
+ *                        and u = (f + 1/2) * 2^-23, exact in FP32.
+ * Both uniforms lie strictly inside (0, 1).
  * Sample:  x_i = lo_i + (c_i + u) * w_i, with c_i the cell's lattice
  *          coordinate at level L and w_i = (hi_i - lo_i) / k^L.
  */
@@ -76,11 +79,44 @@ double zmc_oracle_uniform64(uint32_t w) {
     return ((double)w + 0.5) * (1.0 / 4294967296.0);
 }
 
-/* The uniform of one 32-bit word as the FP32-evaluation mode reads it: the
- * top 23 bits k = w >> 9 give (k + 1/2) / 2^23, exact in FP32.  Returned in a
- * double (the value is exactly representable in both). */
-double zmc_oracle_uniform32(uint32_t w) {
-    return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0);
+/* The FP32-evaluation stream packs five 23-bit fields into each block: read
+ * the block as the 128-bit integer B = w0 + 2^32 w1 + 2^64 w2 + 2^96 w3;
+ * field f (0..4) is bits [23 f, 23 f + 23) of B, and its uniform is
+ * (field + 1/2) / 2^23. */
+uint32_t zmc_oracle_field23(const uint32_t w[4], int f) {
+    uint32_t out = 0;
+    for (int b = 0; b < 23; ++b) {
+        const int bit = 23 * f + b;
+        const uint32_t v = (w[bit / 32] >> (bit % 32)) & 1u;
+        out |= v << b;
+    }
+    return out;
+}
+
+double zmc_oracle_field_uniform(uint32_t field) {
+    return ((double)field + 0.5) * (1.0 / 8388608.0);
+}
+
+/* Uniforms of the (level, slot, trial) stream for points [s0, s0 + count),
+ * all d dimensions, point-major: out[(s - s0)*d + i].
+ *   fp32 = 0: dimension i of points 4g..4g+3 is word (s mod 4) of the block
+ *             with counter (g d + i, t, q, L), uniform (w + 1/2) / 2^32;
+ *   fp32 = 1: dimension i of points 5g..5g+4 is field (s mod 5) of the
+ *             block with counter (g d + i, t, q, L), uniform (f + 1/2) / 2^23. */
+void zmc_oracle_stream_uniforms(uint64_t seed, int level, uint32_t slot, uint32_t trial,
+                                int d, int fp32, int64_t s0, int64_t count, double* out) {
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    const int G = fp32 ? 5 : 4;
+    for (int64_t s = s0; s < s0 + count; ++s) {
+        for (int i = 0; i < d; ++i) {
+            uint32_t ctr[4] = {(uint32_t)((s / G) * d + i), trial, slot, (uint32_t)level};
+            uint32_t w[4];
+            zmc_oracle_philox4x32_10(ctr, key, w);
+            out[(s - s0) * d + i] =
+                fp32 ? zmc_oracle_field_uniform(zmc_oracle_field23(w, (int)(s % G)))
+                     : zmc_oracle_uniform64(w[s % G]);
+        }
+    }
 }
 
 /* Fill `out` with the words of the (level, slot, trial) stream for samples
@@ -193,19 +229,21 @@ static void one_cell_trial(const sums_job* J, int64_t cell, int trial) {
     uint32_t words[64][4];
     double S1 = 0.0, S2 = 0.0;
     const int64_t* c = J->coords + cell * d;
+    /* points per block: 4 words (FP64 stream) or 5 fields (FP32 stream) */
+    const int G = J->fp32_uniforms ? 5 : 4;
     for (int64_t s = 0; s < J->n; ++s) {
-        if (s % 4 == 0) {
-            /* the d Philox blocks that carry samples s .. s+3 */
+        if (s % G == 0) {
+            /* the d Philox blocks that carry samples s .. s+G-1 */
             for (int i = 0; i < d; ++i) {
-                uint32_t ctr[4] = {(uint32_t)((s / 4) * d + i), (uint32_t)trial,
+                uint32_t ctr[4] = {(uint32_t)((s / G) * d + i), (uint32_t)trial,
                                    J->slots[cell], (uint32_t)J->level};
                 zmc_oracle_philox4x32_10(ctr, key, words[i]);
             }
         }
         for (int i = 0; i < d; ++i) {
-            uint32_t w = words[i][s % 4];
-            double u = J->fp32_uniforms ? zmc_oracle_uniform32(w)
-                                        : zmc_oracle_uniform64(w);
+            double u = J->fp32_uniforms
+                           ? zmc_oracle_field_uniform(zmc_oracle_field23(words[i], (int)(s % G)))
+                           : zmc_oracle_uniform64(words[i][s % G]);
             x[i] = J->lo[i] + ((double)c[i] + u) * J->width[i];
         }
         double f = zmc_oracle_integrand(J->integrand, d, x, J->params);
@@ -231,8 +269,8 @@ static void* sums_worker(void* arg) {
 
 /* For each requested cell of one level and each trial, the sums (S1, S2).
  * width[i] = (hi_i - lo_i) / k^level.  Returns 0, or -1 on bad arguments.
- * fp32_uniforms selects the uniform reading of the FP32-evaluation mode
- * (everything else stays FP64). */
+ * fp32_uniforms selects the FP32-evaluation stream (five 23-bit fields per
+ * block): the points the FP32 modes sample; everything else stays FP64. */
 int zmc_oracle_cell_sums(uint64_t seed, int level, int d, const double* lo,
                          const double* width, int64_t n, int trials,
                          int integrand, const double* params, int64_t n_cells,

@@ -86,8 +86,14 @@ def _load():
         lib.zmc_oracle_philox4x32_10.restype = None
         lib.zmc_oracle_uniform64.argtypes = [ctypes.c_uint32]
         lib.zmc_oracle_uniform64.restype = ctypes.c_double
-        lib.zmc_oracle_uniform32.argtypes = [ctypes.c_uint32]
-        lib.zmc_oracle_uniform32.restype = ctypes.c_double
+        lib.zmc_oracle_field23.argtypes = [ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]
+        lib.zmc_oracle_field23.restype = ctypes.c_uint32
+        lib.zmc_oracle_field_uniform.argtypes = [ctypes.c_uint32]
+        lib.zmc_oracle_field_uniform.restype = ctypes.c_double
+        lib.zmc_oracle_stream_uniforms.argtypes = [
+            ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
+            ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
+        lib.zmc_oracle_stream_uniforms.restype = None
         lib.zmc_oracle_integrand.argtypes = [
             ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
             ctypes.POINTER(ctypes.c_double)]
@@ -149,9 +155,27 @@ def uniform64(w: int) -> float:
     return _load().zmc_oracle_uniform64(int(w))
 
 
-def uniform32(w: int) -> float:
-    """(floor(w / 2^9) + 1/2) / 2^23: the FP32-mode uniform of one word."""
-    return _load().zmc_oracle_uniform32(int(w))
+def field23(block, f: int) -> int:
+    """Bits [23 f, 23 f + 23) of a Philox block read as a 128-bit integer."""
+    w = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in block])
+    return _load().zmc_oracle_field23(w, int(f))
+
+
+def field_uniform(field: int) -> float:
+    """(f + 1/2) / 2^23: the FP32-stream uniform of a 23-bit field."""
+    return _load().zmc_oracle_field_uniform(int(field))
+
+
+def stream_uniforms(seed: int, level: int, slot: int, trial: int, d: int, fp32: bool,
+                    s0: int, count: int) -> np.ndarray:
+    """Uniforms of points [s0, s0 + count) of the (level, slot, trial) stream,
+    shape (count, d): the FP64 stream (four 32-bit words per block) or the
+    FP32 stream (five 23-bit fields per block)."""
+    lib = _load()
+    out = np.zeros(count * d, dtype=np.float64)
+    lib.zmc_oracle_stream_uniforms(seed, level, slot, trial, d, 1 if fp32 else 0, s0, count,
+                                   _ptr(out, ctypes.c_double))
+    return out.reshape(count, d)
 
 
 def integrand_value(name: str, x, params) -> float:

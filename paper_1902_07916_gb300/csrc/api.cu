@@ -527,7 +527,7 @@ int run_traced(zmc_ctx* h, cudaStream_t s) {
             tl.parents_out.resize((size_t)tl.flagged * h->dim);
             const uint32_t* next = h->buf.parents[(L + 1) & 1];
             // the statistics kernel left each tile's total in its first unit slot
-            const int64_t chunks = unit_chunks(tl.cells * h->T, (h->n + 3) / 4);
+            const int64_t chunks = unit_chunks(tl.cells * h->T, groups_of(h->n, h->mode));
             e = cudaMemcpy2D(tl.sums.data(), sizeof(double2), h->buf.sums,
                              sizeof(double2) * (size_t)chunks, sizeof(double2),
                              (size_t)tl.cells * h->T, cudaMemcpyDeviceToHost);
@@ -895,6 +895,21 @@ ZMC_API int zmc_run_info(zmc_handle h, int64_t* kernels, int64_t* h2d_bytes, int
     if (kernels) *kernels = h->graph_kernels;
     if (h2d_bytes) *h2d_bytes = (int64_t)sizeof(Desc);
     if (d2h_bytes) *d2h_bytes = (int64_t)sizeof(zmc_result);
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_uniforms(uint64_t seed, int level, uint32_t slot, uint32_t trial, int dim,
+                         int mode, int64_t first, int64_t count, double* out, void* stream) {
+    if (level < 1 || dim < 1 || dim > ZMC_MAX_DIM || first < 0 || count < 0 ||
+        (count > 0 && !out) ||
+        (mode != ZMC_FP64 && mode != ZMC_FP32_FP64ACC && mode != ZMC_FP32_KAHAN))
+        return fail(nullptr, ZMC_ERR_ARG, "bad arguments");
+    const int G = points_per_block(mode);
+    if (((first + count + G - 1) / G) * dim > 0xFFFFFFFFll)
+        return fail(nullptr, ZMC_ERR_ARG, "points beyond the 2^32-block counter range");
+    cudaError_t e = launch_uniforms(seed, level, slot, trial, dim, mode, first, count, out,
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "uniforms launch");
     return ZMC_OK;
 }
 

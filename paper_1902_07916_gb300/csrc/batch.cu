@@ -26,7 +26,7 @@ __global__ void zmc_batch_plan(const BatchEval* __restrict__ items, int count, i
         int64_t units = 0;
         if (C > 0) {
             const int64_t tiles = C * D.T;
-            units = tiles * unit_chunks(tiles, (D.n + 3) >> 2);
+            units = tiles * unit_chunks(tiles, groups_of(D.n, D.mode));
         }
         offsets[i + 1] = units;
     }
@@ -80,7 +80,7 @@ zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
         }
         const BatchEval& it = items[lo];
         const Desc& D = *it.desc;
-        const UnitPlan plan = unit_plan(D, it.st->cells[level]);
+        const UnitPlan plan = unit_plan<MODE>(D, it.st->cells[level]);
         const int64_t local = u - offsets[lo];
         const Unit un = unit_of(plan, local);
         if (lane < D.d) s_pb[warp][lane] = (R)D.pb[lane];

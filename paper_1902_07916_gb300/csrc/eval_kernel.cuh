@@ -1,17 +1,18 @@
 // Kernel (a): the fused sample-generate / evaluate / reduce kernel.
 //
-// Work is cut into units: a unit is a contiguous range of the four-point
-// groups of one (cell, trial) tile (unit_chunks() units per tile).  Every warp
-// walks the level's units persistently and independently (unit += number of
-// warps in the grid); the level's cell count is read from device memory, so
-// the host never needs it.  Per unit:
+// Work is cut into units: a unit is a contiguous range of the point groups
+// of one (cell, trial) tile (unit_chunks() units per tile).  Every warp walks
+// the level's units persistently and independently (unit += number of warps
+// in the grid); the level's cell count is read from device memory, so the
+// host never needs it.  Per unit:
 //   1. lanes < d decode the cell's lattice coordinates from the slot index
 //      (level 1: base-k digits; deeper: parent coordinates * k + child digit)
 //      and fold the cell's geometry into the integrand's per-dimension
 //      coefficients, in the warp's slice of shared memory;
-//   2. every lane takes groups of four consecutive samples; for each
-//      dimension one Philox4x32-10 block (counter (g*d + i, t, q, L)) gives
-//      that dimension's coordinate for all four samples (Sec. 2.2: random
+//   2. every lane takes groups of G consecutive samples (G = 4 in FP64, 5 in
+//      the FP32 modes); for each dimension one Philox4x32-10 block (counter
+//      (g*d + i, t, q, L)) gives that dimension's coordinate for all G
+//      samples -- four 32-bit words or five 23-bit fields (Sec. 2.2: random
 //      numbers are produced where they are used, nothing is stored);
 //   3. f and f^2 are summed per lane, then across the warp with shuffles, and
 //      lane 0 writes the unit's (S1, S2) to the partial-sum array.  The
@@ -21,13 +22,13 @@
 //
 // The dimension loop is compiled for every d in 1..16 (a switch picks the
 // copy once per unit) and unrolled, so the Philox chains of successive
-// dimensions interleave.  Registry integrands fold each coordinate into four
+// dimensions interleave.  Registry integrands fold each coordinate into G
 // independent accumulators as it is produced; expression integrands
-// (compiled at run time, d fixed) keep the four points' coordinates in
+// (compiled at run time, d fixed) keep the G points' coordinates in
 // registers and evaluate the expression on each.
 //
 // MODE 0: FP64 throughout.  MODE 1: FP32 points and integrand, FP32 partial
-// sums over 16 groups (64 points) flushed into FP64 per-lane sums, FP64 warp
+// sums over 16 groups (80 points) flushed into FP64 per-lane sums, FP64 warp
 // reduction.  MODE 2: FP32 points and integrand with TwoSum-compensated
 // per-lane sums and a TwoSum warp reduction; the (sum, error) float pair is
 // widened to FP64 only for the stored result.
@@ -58,11 +59,22 @@ struct ModeTraits<ZMC_FP64> {
     using R2 = double2;
 };
 
-// The assembled 1.m value of a word in the mode's precision.
+// Points per block (and per group) of the mode's stream: 4 or 5.
 template <int MODE>
-__device__ __forceinline__ typename ModeTraits<MODE>::R unit_point(uint32_t w) {
-    if constexpr (MODE == ZMC_FP64) return one_plus_word_f64(w);
-    else return one_plus_word_f32(w);
+constexpr int kGroup = MODE == ZMC_FP64 ? 4 : 5;
+
+// The G assembled 1.m values of one block: four 32-bit words (FP64 stream)
+// or five 23-bit fields (FP32 stream).
+template <int MODE>
+__device__ __forceinline__ void block_points(uint4 w, typename ModeTraits<MODE>::R (&v)[kGroup<MODE>]) {
+    if constexpr (MODE == ZMC_FP64) {
+        v[0] = one_plus_word_f64(w.x);
+        v[1] = one_plus_word_f64(w.y);
+        v[2] = one_plus_word_f64(w.z);
+        v[3] = one_plus_word_f64(w.w);
+    } else {
+        fields_1m(w, v[0], v[1], v[2], v[3], v[4]);
+    }
 }
 
 // Per-lane running sums of f and f^2 in the mode's arithmetic.  MODE 1 keeps
@@ -78,19 +90,27 @@ struct LaneSums {
         if constexpr (MODE == ZMC_FP32_FP64ACC) *slot = make_double2(0.0, 0.0);
     }
 
+    // One group's values: four (FP64) or five (FP32) points.
     template <typename R>
-    __device__ __forceinline__ void add4(R f0, R f1, R f2, R f3) {
+    __device__ __forceinline__ void add(const R (&f)[kGroup<MODE>]) {
         if constexpr (MODE == ZMC_FP64) {
-            S1d += f0; S1d += f1; S1d += f2; S1d += f3;
-            S2d = fma(f0, f0, S2d); S2d = fma(f1, f1, S2d);
-            S2d = fma(f2, f2, S2d); S2d = fma(f3, f3, S2d);
-        } else if constexpr (MODE == ZMC_FP32_FP64ACC) {
-            s1 += (f0 + f1) + (f2 + f3);
-            s2 += fmaf(f0, f0, f1 * f1) + fmaf(f2, f2, f3 * f3);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                S1d += f[j];
+                S2d = fma(f[j], f[j], S2d);
+            }
         } else {
-            float t, r;
-            two_sum(s1, (f0 + f1) + (f2 + f3), t, r); s1 = t; e1 += r;
-            two_sum(s2, fmaf(f0, f0, f1 * f1) + fmaf(f2, f2, f3 * f3), t, r); s2 = t; e2 += r;
+            const float g1 = ((f[0] + f[1]) + (f[2] + f[3])) + f[4];
+            const float g2 = fmaf(f[4], f[4], fmaf(f[0], f[0], f[1] * f[1]) +
+                                                  fmaf(f[2], f[2], f[3] * f[3]));
+            if constexpr (MODE == ZMC_FP32_FP64ACC) {
+                s1 += g1;
+                s2 += g2;
+            } else {
+                float t, r;
+                two_sum(s1, g1, t, r); s1 = t; e1 += r;
+                two_sum(s2, g2, t, r); s2 = t; e2 += r;
+            }
         }
     }
 
@@ -135,13 +155,13 @@ struct LaneSums {
 };
 
 // Mask the points past n in the tile's last group (only it can be short):
-// `tail` is the number of real points of that group, 1..4.
-template <typename R>
-__device__ __forceinline__ void mask_tail(bool last, uint32_t tail, R& f1, R& f2, R& f3) {
+// `tail` is the number of real points of that group, 1..G.
+template <typename R, int G>
+__device__ __forceinline__ void mask_tail(bool last, uint32_t tail, R (&f)[G]) {
     if (last) {
-        if (tail < 4) f3 = R(0);
-        if (tail < 3) f2 = R(0);
-        if (tail < 2) f1 = R(0);
+#pragma unroll
+        for (int j = 1; j < G; ++j)
+            if ((uint32_t)j >= tail) f[j] = R(0);
     }
 }
 
@@ -152,11 +172,12 @@ struct UnitPlan {
     int T;
 };
 
+template <int MODE>
 __device__ __forceinline__ UnitPlan unit_plan(const Desc& D, int64_t C) {
     UnitPlan p;
     p.T = D.T;
-    p.ngroups = (uint32_t)((D.n + 3) >> 2);                 // < 2^32: n * d < 2^34
-    p.tail = (uint32_t)(D.n - 4 * (int64_t)(p.ngroups - 1));
+    p.ngroups = (uint32_t)groups_of(D.n, MODE);             // < 2^32: n * d < 2^34
+    p.tail = (uint32_t)(D.n - (int64_t)kGroup<MODE> * (int64_t)(p.ngroups - 1));
     const int64_t tiles = C * D.T;
     p.chunks = unit_chunks(tiles, p.ngroups);
     p.units = tiles * p.chunks;
@@ -233,9 +254,12 @@ __device__ __forceinline__ void sample_unit_fold(
     const uint64_t step = (uint64_t)kPhiloxMulA * (uint64_t)(32 * nd);
     uint32_t g = g0 + (threadIdx.x & 31);
     uint64_t Pg = (uint64_t)kPhiloxMulA * (uint64_t)(g * nd);
+    constexpr int G = kGroup<MODE>;
     while (g < g1) {
         for (int j = 0; j < kFlushGroups && g < g1; ++j, g += 32, Pg += step) {
-            R a0 = start, a1 = start, a2 = start, a3 = start;
+            R a[G];
+#pragma unroll
+            for (int p = 0; p < G; ++p) a[p] = start;
             uint64_t P = Pg;
 #pragma unroll kDimUnroll
             for (int i = 0; i < nd; ++i) {
@@ -243,15 +267,16 @@ __device__ __forceinline__ void sample_unit_fold(
                 P += kPhiloxMulA;
                 const R2 ab = w_coef[i];
                 const R pb = s_pb[i];
-                a0 = F::fold(a0, unit_point<MODE>(w.x), ab.x, ab.y, pb);
-                a1 = F::fold(a1, unit_point<MODE>(w.y), ab.x, ab.y, pb);
-                a2 = F::fold(a2, unit_point<MODE>(w.z), ab.x, ab.y, pb);
-                a3 = F::fold(a3, unit_point<MODE>(w.w), ab.x, ab.y, pb);
+                R v[G];
+                block_points<MODE>(w, v);
+#pragma unroll
+                for (int p = 0; p < G; ++p) a[p] = F::fold(a[p], v[p], ab.x, ab.y, pb);
             }
-            R f0 = F::template finish<WIDE>(a0, s_c, nd), f1 = F::template finish<WIDE>(a1, s_c, nd);
-            R f2 = F::template finish<WIDE>(a2, s_c, nd), f3 = F::template finish<WIDE>(a3, s_c, nd);
-            mask_tail(g == last_group, tail, f1, f2, f3);
-            acc.add4(f0, f1, f2, f3);
+            R f[G];
+#pragma unroll
+            for (int p = 0; p < G; ++p) f[p] = F::template finish<WIDE>(a[p], s_c, nd);
+            mask_tail(g == last_group, tail, f);
+            acc.add(f);
         }
         acc.flush();
     }
@@ -278,7 +303,7 @@ zmc_eval_reduce(const Desc* __restrict__ desc, const State* __restrict__ st,
     if (tid < 4) s_c[tid] = (R)D.c[tid];
     __syncthreads();
 
-    const UnitPlan plan = unit_plan(D, C);
+    const UnitPlan plan = unit_plan<MODE>(D, C);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     double2* slot = &s_acc[MODE == ZMC_FP32_FP64ACC ? tid : 0];
     for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; u < plan.units; u += nwarps) {
@@ -329,10 +354,11 @@ __device__ __forceinline__ void eval_expr_body(const Desc* __restrict__ desc,
     if (tid < 4) s_p[2 * ZMC_MAX_DIM + tid] = (R)D.c[tid];
     __syncthreads();
 
-    const UnitPlan plan = unit_plan(D, C);
+    const UnitPlan plan = unit_plan<MODE>(D, C);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     double2* slot = &s_acc[MODE == ZMC_FP32_FP64ACC ? tid : 0];
     R2* wb = s_wb[warp];
+    constexpr int G = kGroup<MODE>;
     for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; u < plan.units; u += nwarps) {
         const Unit un = unit_of(plan, u);
         if (lane < DIM) {
@@ -346,21 +372,22 @@ __device__ __forceinline__ void eval_expr_body(const Desc* __restrict__ desc,
         uint32_t g = un.g0 + lane;
         while (g < un.g1) {
             for (int j = 0; j < kFlushGroups && g < un.g1; ++j, g += 32) {
-                R x0[DIM], x1[DIM], x2[DIM], x3[DIM];
+                R x[G][DIM];
                 const uint32_t cbase = g * DIM;
 #pragma unroll
                 for (int i = 0; i < DIM; ++i) {
                     const uint4 w = philox_stream(keys, sc, cbase + i);
                     const R2 c = wb[i];
-                    x0[i] = fma(unit_point<MODE>(w.x), c.x, c.y);
-                    x1[i] = fma(unit_point<MODE>(w.y), c.x, c.y);
-                    x2[i] = fma(unit_point<MODE>(w.z), c.x, c.y);
-                    x3[i] = fma(unit_point<MODE>(w.w), c.x, c.y);
+                    R v[G];
+                    block_points<MODE>(w, v);
+#pragma unroll
+                    for (int p = 0; p < G; ++p) x[p][i] = fma(v[p], c.x, c.y);
                 }
-                R f0 = E::eval(x0, s_p), f1 = E::eval(x1, s_p);
-                R f2 = E::eval(x2, s_p), f3 = E::eval(x3, s_p);
-                mask_tail(g == plan.ngroups - 1, plan.tail, f1, f2, f3);
-                acc.add4(f0, f1, f2, f3);
+                R f[G];
+#pragma unroll
+                for (int p = 0; p < G; ++p) f[p] = E::eval(x[p], s_p);
+                mask_tail(g == plan.ngroups - 1, plan.tail, f);
+                acc.add(f);
             }
             acc.flush();
         }

@@ -158,7 +158,7 @@ __device__ __forceinline__ void cell_stats_body(const Desc* __restrict__ desc, S
     // The sampling kernel left unit_chunks() partial sums per (cell, trial)
     // tile, contiguous per tile; add them in order and keep the total in the
     // tile's first slot.
-    const int64_t chunks = unit_chunks(C * T, (D.n + 3) >> 2);
+    const int64_t chunks = unit_chunks(C * T, groups_of(D.n, D.mode));
     bool finite = true;
     Moments acc{0.0, 0.0, 0.0};
     for (int64_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
@@ -454,6 +454,43 @@ __global__ void zmc_philox_fill(const PhiloxKeys keys, uint32_t c0, uint32_t c1,
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < count;
          b += (int64_t)gridDim.x * blockDim.x)
         out[b] = philox_stream(keys, sc, c0 + (uint32_t)b);
+}
+
+// The uniforms of points [first, first + count) of one (level, slot, trial)
+// stream, all d dimensions, as the sampling kernel forms them (1.m values
+// from philox_stream, block_points' field layout), minus the exact shift.
+__global__ void zmc_uniforms_fill(const PhiloxKeys keys, uint32_t level, uint32_t slot,
+                                  uint32_t trial, int d, int mode, int64_t first, int64_t count,
+                                  double* out) {
+    const StreamConst sc = stream_const(keys, trial, slot, level);
+    const int G = mode == ZMC_FP64 ? 4 : 5;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count * d;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = first + e / d;
+        const int i = (int)(e % d);
+        const uint4 w = philox_stream(keys, sc, (uint32_t)((s / G) * d + i));
+        const int lane = (int)(s % G);
+        double u;
+        if (mode == ZMC_FP64) {
+            const uint32_t word = lane == 0 ? w.x : lane == 1 ? w.y : lane == 2 ? w.z : w.w;
+            u = one_plus_word_f64(word) - (1.0 - 0x1p-33);
+        } else {
+            float v[5];
+            fields_1m(w, v[0], v[1], v[2], v[3], v[4]);
+            u = (double)(v[lane] - (1.0f - 0x1p-24f));
+        }
+        out[e] = u;
+    }
+}
+
+cudaError_t launch_uniforms(uint64_t seed, int level, uint32_t slot, uint32_t trial, int d,
+                            int mode, int64_t first, int64_t count, double* out, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count * d + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    zmc_uniforms_fill<<<(int)blocks, 256, 0, s>>>(philox_keys(seed), (uint32_t)level, slot,
+                                                  trial, d, mode, first, count, out);
+    return cudaGetLastError();
 }
 
 PhiloxKeys philox_keys(uint64_t seed) {

@@ -71,20 +71,31 @@ __device__ __forceinline__ uint4 philox_stream(const PhiloxKeys& K, const Stream
 }
 
 // ------------------------------------------------------ word -> point maps
-// The stream of (level L, slot q, trial t): dimension i of samples 4g..4g+3
-// is the block with counter (g*d + i, t, q, L), one lane per sample.
+// The stream of (level L, slot q, trial t): dimension i of samples
+// G g .. G g + G - 1 is the block with counter (g*d + i, t, q, L); G = 4 in
+// the FP64 stream (one 32-bit word per sample), 5 in the FP32 stream.
 //
-// FP64 reading: u = (w + 1/2) 2^-32.  The double 1 + w 2^-32 is assembled
+// FP64 stream: u = (w + 1/2) 2^-32.  The double 1 + w 2^-32 is assembled
 // from the word's bits, and the point lo + (c + u) w_L is formed from it as
 // w_L * (1 + w 2^-32) + (lo + c w_L - (1 - 2^-33) w_L).
 __device__ __forceinline__ double one_plus_word_f64(uint32_t w) {
     return __hiloint2double(0x3FF00000 | (int)(w >> 12), (int)(w << 20));
 }
-// FP32 reading: u = (floor(w / 2^9) + 1/2) 2^-23, exact in binary32; the
-// float 1 + floor(w / 2^9) 2^-23 is assembled from the bits, and the point
-// is w_L * (1.m) + (lo + c w_L - (1 - 2^-24) w_L).
-__device__ __forceinline__ float one_plus_word_f32(uint32_t w) {
-    return __uint_as_float(0x3F800000u | (w >> 9));
+// FP32 stream: a block carries dimension i of FIVE points, as the 23-bit
+// fields f = 0..4 of the block read as a 128-bit integer (bits 23 f ..
+// 23 f + 22); u = (field + 1/2) 2^-23, exact in binary32.  The float
+// 1 + field 2^-23 is assembled from the bits, and the point is
+// w_L * (1.m) + (lo + c w_L - (1 - 2^-24) w_L).
+__device__ __forceinline__ float one_plus_field(uint32_t field23) {
+    return __uint_as_float(0x3F800000u | (field23 & 0x7FFFFFu));
+}
+__device__ __forceinline__ void fields_1m(uint4 w, float& v0, float& v1, float& v2, float& v3,
+                                          float& v4) {
+    v0 = one_plus_field(w.x);                              // bits   0 ..  22
+    v1 = one_plus_field(__funnelshift_r(w.x, w.y, 23));    // bits  23 ..  45
+    v2 = one_plus_field(__funnelshift_r(w.y, w.z, 14));    // bits  46 ..  68
+    v3 = one_plus_field(w.z >> 5);                         // bits  69 ..  91
+    v4 = one_plus_field(__funnelshift_r(w.z, w.w, 28));    // bits  92 .. 114
 }
 
 // ------------------------------------------------ elementary functions

@@ -47,6 +47,9 @@ cudaError_t launch_final(const Buffers& b, cudaStream_t s);
 // Round keys of a seed (host side).
 PhiloxKeys philox_keys(uint64_t seed);
 
+cudaError_t launch_uniforms(uint64_t seed, int level, uint32_t slot, uint32_t trial, int d,
+                            int mode, int64_t first, int64_t count, double* out, cudaStream_t s);
+
 // zmc_level_stats_noalloc (select.cu): returns ZMC_OK or an error code with
 // the message in noalloc_last_error().
 int level_stats_noalloc(const double* sums, int64_t cells, int trials, int64_t n, double volume,

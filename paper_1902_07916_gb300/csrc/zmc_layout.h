@@ -63,12 +63,27 @@ struct State {
 };
 
 // Work units of the sampling kernel.  A (cell, trial) tile is cut into
-// `chunks` units of about equal numbers of four-point groups so that a level
+// `chunks` units of about equal numbers of point groups so that a level
 // has at least kTargetUnits units when it can, but no unit has fewer than
 // kMinUnitGroups groups.  The count depends only on the level's tile count
 // and on n, never on the GPU, so neither do the results.
 constexpr int64_t kTargetUnits = int64_t(1) << 18;
 constexpr int64_t kMinUnitGroups = 1024;
+
+// Points per Philox block in the mode's stream: four 32-bit words (FP64) or
+// five 23-bit fields (FP32 modes); a "group" is that many consecutive points.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int points_per_block(int mode) { return mode == ZMC_FP64 ? 4 : 5; }
+
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int64_t groups_of(int64_t n, int mode) {
+    const int G = points_per_block(mode);
+    return (n + G - 1) / G;
+}
 
 #ifdef __CUDACC__
 __host__ __device__

@@ -105,6 +105,9 @@ def _load():
         "zmc_philox_words": [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                              ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
                              ctypes.c_void_p, ctypes.c_void_p],
+        "zmc_uniforms": [ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
+                         ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                         ctypes.c_void_p, ctypes.c_void_p],
         "zmc_set_profiling": [H, ctypes.c_int],
         "zmc_profile": [H, P(ctypes.c_double), P(ctypes.c_int)],
         "zmc_run_info": [H, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)],
@@ -238,6 +241,14 @@ def zmc_philox_words(seed, c0, c1, c2, c3, count, out_ptr, stream=None):
                                  c1 & 0xFFFFFFFF, c2 & 0xFFFFFFFF, c3 & 0xFFFFFFFF,
                                  int(count), ctypes.c_void_p(int(out_ptr)),
                                  _stream_ptr(stream)))
+
+
+def zmc_uniforms(seed, level, slot, trial, dim, mode, first, count, out_ptr, stream=None):
+    if isinstance(mode, str):
+        mode = PRECISIONS[mode]
+    _check(_lib.zmc_uniforms(int(seed) & 0xFFFFFFFFFFFFFFFF, int(level), int(slot) & 0xFFFFFFFF,
+                             int(trial) & 0xFFFFFFFF, int(dim), int(mode), int(first),
+                             int(count), ctypes.c_void_p(int(out_ptr)), _stream_ptr(stream)))
 
 
 def zmc_set_profiling(h, on: bool):

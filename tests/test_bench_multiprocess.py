@@ -29,7 +29,8 @@ rank = dist.get_rank(); world = dist.get_world_size()
 # rank r timed 100*(r+1) ms for 1000*(r+1) points
 t, total, value = bench.weak_scaling_value(world, 100.0 * (rank + 1), 1000.0 * (rank + 1))
 bench.barrier(world)
-print(json.dumps({{"rank": rank, "t": t, "total": total, "value": value}}))
+with open(os.path.join({out!r}, "rank%d.json" % rank), "w") as fh:
+    json.dump({{"rank": rank, "t": t, "total": total, "value": value}}, fh)
 dist.destroy_process_group()
 """
 
@@ -47,11 +48,10 @@ def _torchrun(script_args, env_extra=None, nproc=2, timeout=240):
 def test_weak_scaling_aggregation_two_gloo_ranks(tmp_path):
     pytest.importorskip("torch")
     script = tmp_path / "worker.py"
-    script.write_text(WORKER.format(root=ROOT))
+    script.write_text(WORKER.format(root=ROOT, out=str(tmp_path)))
     r = _torchrun([str(script)])
     assert r.returncode == 0, r.stderr[-2000:]
-    lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
-    assert len(lines) == 2
+    lines = [json.loads((tmp_path / ("rank%d.json" % k)).read_text()) for k in range(2)]
     for x in lines:
         # slowest rank 200 ms; 3000 points in total
         assert x["t"] == 200.0 and x["total"] == 3000.0

@@ -54,6 +54,24 @@ def test_philox_words_bit_exact(zmc, seed, ctr):
         assert np.array_equal(got[b], O.philox4x32_10(c, key)), b
 
 
+@pytest.mark.parametrize("mode", ["fp64", "fp32_fp64acc"])
+@pytest.mark.parametrize("seed,level,slot,trial,dim,first,count", [
+    (0, 1, 0, 0, 1, 0, 97), (0xC0FFEE, 2, 12345, 7, 6, 3, 211),
+    (2**64 - 1, 4, 2**32 - 1, 2**32 - 1, 16, 1001, 64), (7, 3, 5, 1, 9, 0, 5),
+])
+def test_uniforms_bit_exact(zmc, mode, seed, level, slot, trial, dim, first, count):
+    # both streams (four 32-bit words / five 23-bit fields per block), for
+    # ragged starting points and every dimension, against the oracle
+    import torch
+    out = torch.full((count * dim,), float("nan"), dtype=torch.float64, device="cuda")
+    zmc.zmc_uniforms(seed, level, slot, trial, dim, mode, first, count, out.data_ptr(),
+                     torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(count, dim)
+    ref = O.stream_uniforms(seed, level, slot, trial, dim, mode != "fp64", first, count)
+    assert np.array_equal(got, ref)
+
+
 # ---------------------------------------------------- FP64 full parity
 
 def W(name, integrand, d, a, b, k, n, T, depth, m, seed, params=(), **kw):

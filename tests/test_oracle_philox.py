@@ -96,13 +96,47 @@ def test_uniform64_exact_and_open(oracle, w):
     assert 0.0 < u < 1.0
 
 
-@pytest.mark.parametrize("w", [0, 511, 512, 2**31, 2**32 - 1, 0x89ABCDEF])
-def test_uniform32_exact_and_open(oracle, w):
-    u = oracle.uniform32(w)
-    assert Fraction(u) == Fraction(2 * (w >> 9) + 1, 2**24)
+@pytest.mark.parametrize("block", [(0, 0, 0, 0), (0xFFFFFFFF,) * 4,
+                                   (0x12345678, 0x9ABCDEF0, 0x0F1E2D3C, 0x4B5A6978),
+                                   (1, 1 << 31, 0x80000001, 0x7FFFFFFF)])
+def test_field23_is_the_128_bit_slice(oracle, block):
+    # the block read as one little-endian 128-bit integer, sliced 23 bits at a time
+    B = sum(int(w) << (32 * j) for j, w in enumerate(block))
+    for f in range(5):
+        assert oracle.field23(block, f) == (B >> (23 * f)) & ((1 << 23) - 1)
+
+
+@pytest.mark.parametrize("field", [0, 1, 2**22, 2**23 - 2, 2**23 - 1, 0x5A5A5A])
+def test_field_uniform_exact_and_open(oracle, field):
+    u = oracle.field_uniform(field)
+    assert Fraction(u) == Fraction(2 * field + 1, 2**24)
     assert 0.0 < u < 1.0
-    # exactly representable in binary32
-    assert float(np.float32(u)) == u
+    assert float(np.float32(u)) == u          # exactly representable in binary32
+
+
+def test_fp32_stream_layout(oracle):
+    # point s, dimension i of the FP32 stream is field s % 5 of the block with
+    # counter ((s // 5) * d + i, trial, slot, level)
+    seed, level, slot, trial, d = 0x5EED, 2, 41, 3, 3
+    u = oracle.stream_uniforms(seed, level, slot, trial, d, True, 7, 12)
+    key = oracle.seed_key(seed)
+    for r, s in enumerate(range(7, 19)):
+        for i in range(d):
+            blk = oracle.philox4x32_10(((s // 5) * d + i, trial, slot, level), key)
+            assert u[r, i] == oracle.field_uniform(oracle.field23(blk, s % 5))
+    # and the FP64 stream reads whole words, four points per block
+    u64 = oracle.stream_uniforms(seed, level, slot, trial, d, False, 7, 12)
+    w = oracle.stream_words(seed, level, slot, trial, d, 7, 12)
+    assert np.array_equal(u64, (w.astype(np.float64) + 0.5) / 2**32)
+
+
+def test_fp32_stream_statistics(oracle):
+    u = oracle.stream_uniforms(77, 1, 5, 0, 4, True, 0, 50000).ravel()
+    N = u.size
+    assert abs(u.mean() - 0.5) < 5 * math.sqrt(1 / 12 / N)
+    assert abs(u.var() - 1 / 12) < 5 * math.sqrt(1 / 180 / N)
+    c = np.corrcoef(u[:-1], u[1:])[0, 1]
+    assert abs(c) < 5 / math.sqrt(N)
 
 
 def test_uniform_statistics(oracle):
