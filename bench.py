@@ -165,14 +165,15 @@ class ClockSampler:
 
 # --------------------------------------------------------- our arm
 
-def philox_multiplies_per_sample(d: int) -> float:
-    """Algorithmic integer work per point: one Philox4x32-10 block per four
-    points and dimension.  A block is ten rounds of two 32x32->64-bit
-    products; of those twenty, the two that depend only on (trial, slot,
-    level) are taken once per stream and round 1's product of the block
-    counter is an arithmetic progression (additions), which leaves 17 wide
-    multiplies per block."""
-    return d / 4.0 * 17
+def philox_multiplies_per_sample(d: int, fp64: bool) -> float:
+    """Algorithmic integer work per point: one Philox4x32-10 block per
+    dimension and group of points (four 32-bit words in the FP64 stream, five
+    23-bit fields in the FP32 stream).  A block is ten rounds of two
+    32x32->64-bit products; of those twenty, the two that depend only on
+    (trial, slot, level) are taken once per stream and round 1's product of
+    the block counter is an arithmetic progression (additions), which leaves
+    17 wide multiplies per block."""
+    return d / (4.0 if fp64 else 5.0) * 17
 
 
 # Wide (32x32->64-bit) integer multiplies per SM per clock on this GPU: the
@@ -229,7 +230,7 @@ def run_ours(args, world, rank, local):
     t_max, all_samples, value = weak_scaling_value(world, total_ms, float(sum(samples)))
 
     # roofline of the dominant kernel (the sampling kernel)
-    ops = sum(samples) * philox_multiplies_per_sample(w.dim)
+    ops = sum(samples) * philox_multiplies_per_sample(w.dim, prec == zmc.ZMC_FP64)
     eval_s = sum(eval_ms) * 1e-3
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = clk.get("sm_max_mhz") or 2070.0
@@ -307,7 +308,7 @@ def run_ours(args, world, rank, local):
             "frac": round(achieved / peak, 4),
             "peak_basis": "%d IMAD.WIDE/clk/SM x %d SMs x %.0f MHz (max SM clock)" % (
                 WIDE_MULS_PER_SM_CLK, sms, max_mhz),
-            "work_per_sample": philox_multiplies_per_sample(w.dim),
+            "work_per_sample": philox_multiplies_per_sample(w.dim, prec == zmc.ZMC_FP64),
             "kernel_ms_per_step": round(sum(eval_ms) / len(eval_ms), 3),
             "kernel_share_of_step": round(sum(eval_ms) / total_ms, 4),
             "traffic": None,
