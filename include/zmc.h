@@ -152,6 +152,20 @@ ZMC_API int zmc_set_limits(zmc_handle h, int64_t max_cells_per_level,
                            int64_t max_samples);
 
 /*
+ * zmc_set_launch -- launch shape of the sampling kernel: `threads` per CTA
+ * (64, 128 or 256) and at most `ctas_per_sm` CTAs per SM (0: as many as fit).
+ * threads = 0 (the default) lets the library's autotuner choose: on the
+ * first run of a (precision, integrand, dimension) it times each candidate
+ * shape once on a truncated level 1 of that problem and keeps the fastest
+ * for the process (ZMC_TUNE=0 in the environment disables it).  Results do
+ * not depend on the shape: the work units and their order of summation are
+ * fixed by the level's size, n and the precision.  Errors: ZMC_ERR_ARG.
+ * zmc_launch_shape reports the shape of the last run (threads per CTA, CTAs).
+ */
+ZMC_API int zmc_set_launch(zmc_handle h, int threads, int ctas_per_sm);
+ZMC_API int zmc_launch_shape(zmc_handle h, int* threads, int* grid);
+
+/*
  * zmc_integrate -- run the whole tree search on the current device and
  * return the result in *out (host).  Copies the handle's parameters to the
  * device, enqueues every level on `stream` (replaying a CUDA graph captured

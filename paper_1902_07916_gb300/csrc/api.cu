@@ -8,8 +8,9 @@
 #include <string.h>
 
 #include <algorithm>
-#include <string>
+#include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "jit.h"
@@ -56,7 +57,7 @@ struct zmc_ctx {
     zmc_result* h_result = nullptr;  // pinned landing zone of the result
     bool desc_dirty = true;
     JitKernel jit{};                 // expression integrand, if any
-    int eval_threads = 256;
+    int launch_threads = 0, launch_per_sm = 0;  // 0: autotuned
     EvalShape shapes[ZMC_MAX_DEPTH + 1] = {};  // per level, set before capture
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -321,24 +322,117 @@ const void* eval_kernel(const zmc_ctx* h) {
     }
 }
 
-EvalShape eval_shape(const zmc_ctx* h, int level) {
-    EvalShape sh;
-    sh.threads = h->eval_threads;
+// ------------------------------------------------------------ autotuner
+// The sampling kernel's results do not depend on its launch shape (the work
+// units and their order of summation depend only on the level's size, n and
+// the precision), so the shape is free to tune.  Candidates: 128 or 256
+// threads per CTA, and from the occupancy limit down to half of it CTAs per
+// SM.  Each is timed once on a truncated level 1 of the caller's own
+// problem (about 2^29 points), the fastest is kept per (kernel, dimension)
+// for the life of the process.  ZMC_TUNE=0 in the environment, or an
+// explicit zmc_set_launch(), skips it.
+struct Tuned {
+    int threads, per_sm;
+};
+std::mutex g_tune_mu;
+std::map<std::pair<const void*, int>, Tuned> g_tuned;
+
+int occupancy(const void* kernel, int threads) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_kernel(h), sh.threads, 0);
-    if (per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)h->num_sms * per_sm;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    return std::max(per_sm, 1);
+}
+
+Tuned default_shape(const zmc_ctx* h) {
+    return Tuned{256, occupancy(eval_kernel(h), 256)};
+}
+
+float time_level1(zmc_ctx* h, Tuned c, int64_t cells, cudaEvent_t e0, cudaEvent_t e1) {
+    cudaStream_t s = h->cap_stream;
+    const Buffers& b = h->buf;
+    const PhiloxKeys keys = philox_keys(h->seed);
+    const uint32_t* parents = b.parents[1];
+    int level = 1;
+    void* args[] = {(void*)&b.desc, (void*)&b.state, (void*)&parents, (void*)&b.sums,
+                    (void*)&level, (void*)&keys};
+    if (launch_init(b, cells, s) != cudaSuccess) return -1.f;
+    cudaEventRecord(e0, s);
+    if (cudaLaunchKernel(eval_kernel(h), dim3(c.per_sm * h->num_sms), dim3(c.threads), args, 0,
+                         s) != cudaSuccess)
+        return -1.f;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+    float ms = -1.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+}
+
+Tuned tuned_shape(zmc_ctx* h) {
+    if (h->launch_threads > 0) {
+        const int occ = occupancy(eval_kernel(h), h->launch_threads);
+        const int per_sm = h->launch_per_sm > 0 ? std::min(h->launch_per_sm, occ) : occ;
+        return Tuned{h->launch_threads, per_sm};
+    }
+    const char* env = getenv("ZMC_TUNE");
+    if (env && strcmp(env, "0") == 0) return default_shape(h);
+    const std::pair<const void*, int> key(eval_kernel(h), h->dim);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) return it->second;
+    }
+    // the descriptor upload was enqueued on the caller's stream
+    if (cudaDeviceSynchronize() != cudaSuccess) return default_shape(h);
+    const int64_t K = ipow_sat(h->k, h->dim, INT64_MAX);
+    const int64_t per_cell = h->n * (int64_t)h->T;
+    const int64_t cells = std::max<int64_t>(1, std::min<int64_t>(K, (int64_t(1) << 29) / per_cell));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return default_shape(h);
+    }
+    std::vector<Tuned> cands;
+    for (int threads : {256, 128}) {
+        const int occ = occupancy(eval_kernel(h), threads);
+        for (int per_sm = occ; per_sm >= std::max(1, occ / 2); --per_sm)
+            cands.push_back(Tuned{threads, per_sm});
+    }
+    Tuned best = cands.front();
+    float best_ms = -1.f;
+    time_level1(h, best, cells, e0, e1);   // warm-up
+    for (const Tuned& c : cands) {
+        const float ms = time_level1(h, c, cells, e0, e1);
+        if (ms > 0.f && (best_ms < 0.f || ms < best_ms)) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[key] = best;
+    return best;
+}
+
+EvalShape eval_shape(zmc_ctx* h, int level, Tuned t) {
+    EvalShape sh;
+    sh.threads = t.threads;
+    int64_t grid = (int64_t)h->num_sms * t.per_sm;
     if (level == 1) {
+        // no more CTAs than level 1 has units for their warps
         const int64_t tiles = ipow_sat(h->k, h->dim, INT64_MAX) * h->T;
-        grid = std::min(grid, tiles);
+        const int64_t units = tiles * unit_chunks(tiles, groups_of(h->n, h->mode));
+        grid = std::min(grid, (units + t.threads / 32 - 1) / (t.threads / 32));
     }
     sh.grid = (int)std::max<int64_t>(grid, 1);
     return sh;
 }
 
-// Occupancy queries happen here, outside any stream capture.
+// Occupancy queries and tuning happen here, outside any stream capture.
 void plan_shapes(zmc_ctx* h) {
-    for (int L = 1; L <= h->depth; ++L) h->shapes[L] = eval_shape(h, L);
+    const Tuned t = tuned_shape(h);
+    for (int L = 1; L <= h->depth; ++L) h->shapes[L] = eval_shape(h, L, t);
 }
 
 cudaError_t enqueue_eval(zmc_ctx* h, int level, const uint32_t* parents_prev, cudaStream_t s) {
@@ -662,6 +756,25 @@ ZMC_API int zmc_set_limits(zmc_handle h, int64_t max_cells, int64_t max_samples)
     h->max_samples = max_samples;
     h->desc_dirty = true;
     h->graph_stale = true;
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_set_launch(zmc_handle h, int threads, int ctas_per_sm) {
+    if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle");
+    if (threads != 0 && threads != 64 && threads != 128 && threads != 256)
+        return fail(h, ZMC_ERR_ARG, "threads must be 0 (tuned), 64, 128 or 256");
+    if (ctas_per_sm < 0) return fail(h, ZMC_ERR_ARG, "ctas_per_sm must be >= 0");
+    h->launch_threads = threads;
+    h->launch_per_sm = ctas_per_sm;
+    h->graph_stale = true;
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_launch_shape(zmc_handle h, int* threads, int* grid) {
+    if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle");
+    if (!h->graph && h->trace_levels.empty()) return fail(h, ZMC_ERR_ARG, "nothing has run yet");
+    if (threads) *threads = h->shapes[1].threads;
+    if (grid) *grid = h->shapes[std::min(2, h->depth)].grid;
     return ZMC_OK;
 }
 

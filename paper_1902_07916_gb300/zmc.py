@@ -108,6 +108,8 @@ def _load():
         "zmc_uniforms": [ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
                          ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
                          ctypes.c_void_p, ctypes.c_void_p],
+        "zmc_set_launch": [H, ctypes.c_int, ctypes.c_int],
+        "zmc_launch_shape": [H, P(ctypes.c_int), P(ctypes.c_int)],
         "zmc_set_profiling": [H, ctypes.c_int],
         "zmc_profile": [H, P(ctypes.c_double), P(ctypes.c_int)],
         "zmc_run_info": [H, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)],
@@ -249,6 +251,16 @@ def zmc_uniforms(seed, level, slot, trial, dim, mode, first, count, out_ptr, str
     _check(_lib.zmc_uniforms(int(seed) & 0xFFFFFFFFFFFFFFFF, int(level), int(slot) & 0xFFFFFFFF,
                              int(trial) & 0xFFFFFFFF, int(dim), int(mode), int(first),
                              int(count), ctypes.c_void_p(int(out_ptr)), _stream_ptr(stream)))
+
+
+def zmc_set_launch(h, threads=0, ctas_per_sm=0):
+    _check(_lib.zmc_set_launch(h, int(threads), int(ctas_per_sm)), h)
+
+
+def zmc_launch_shape(h):
+    t, g = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.zmc_launch_shape(h, ctypes.byref(t), ctypes.byref(g)), h)
+    return t.value, g.value
 
 
 def zmc_set_profiling(h, on: bool):

@@ -151,3 +151,26 @@ def test_expression_compile_error_reports_log(zmc):
         assert "no_such_function" in zmc.zmc_last_error(h)
     finally:
         zmc.zmc_destroy(h)
+
+
+# ------------------------------------------------------- launch shape
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_kahan"])
+def test_results_do_not_depend_on_launch_shape(zmc, precision):
+    w = Workload("corner4", "genz_corner", 4, [0.0] * 4, [1.0] * 4, 3, 3001, 6, 3, 0.5, 5,
+                 [1.0, 2.0, 3.0, 4.0])
+    results = []
+    for threads, per_sm in [(0, 0), (64, 1), (128, 2), (256, 0)]:
+        it = zmc.Integrator(w.dim, w.lo, w.hi, w.k, w.n, w.trials, w.depth,
+                            w.sigma_multiplier, w.seed, w.integrand, w.params,
+                            precision=zmc.PRECISIONS[precision])
+        try:
+            zmc.zmc_set_launch(it.h, threads, per_sm)
+            r = it.integrate()
+            shape = zmc.zmc_launch_shape(it.h)
+            if threads:
+                assert shape[0] == threads
+        finally:
+            it.close()
+        results.append((r.value, r.std, r.flagged_per_level, r.cells_per_level))
+    assert all(x == results[0] for x in results), results
