@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     p.add_argument("--no-batch", action="store_true", help="skip the batched leg")
+    p.add_argument("--no-tta", action="store_true", help="skip the time-to-accuracy leg")
     p.add_argument("--paper", action="store_true",
                    help="run the paper's parameter sets (Sec. 3) instead of the benchmark")
     return p.parse_args()
@@ -277,6 +278,10 @@ def run_ours(args, world, rank, local):
     if rank == 0 and not args.no_batch:
         batched = run_batched(zmc, stream, prec)
 
+    tta = None
+    if rank == 0 and world == 1 and not args.no_tta:
+        tta = run_tta(zmc, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, target_s=12.0)
@@ -319,6 +324,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": kernels_per_run * args.steps,
         "fp64": fp64,
         "batched": batched,
+        "time_to_accuracy": tta,
         "cpu_baseline": cpu,
     }
     return line
@@ -363,6 +369,132 @@ def run_batched(zmc, stream, prec, steps: int = 3):
     finally:
         for h in hs:
             zmc.zmc_destroy(h)
+
+
+# ------------------------------------------------------ time to accuracy
+
+TTA_TARGET = 1e-4
+TTA_SEEDS = 5
+TTA_N = [1 << e for e in range(10, 23)]
+TTA_SWEEP_BUDGET_S = 120.0
+TTA_FP64_BUDGET_S = 75.0
+
+
+def exact_value(w) -> float:
+    """Closed form of a workload whose integrand is a product of (or the sine
+    of a sum of) one-dimensional terms: the normalised Gaussian integrates to
+    a product of erf differences, sin(sum x) to the imaginary part of a
+    product of (e^{i h} - e^{i l}) / i (Eqs. 1-2 of Sec. 3)."""
+    if w.integrand == "gauss_norm":
+        s = w.params[0] * math.sqrt(2.0)
+        return math.prod(0.5 * (math.erf(h / s) - math.erf(l / s)) for l, h in zip(w.lo, w.hi))
+    if w.integrand == "sin_sum":
+        z = complex(1.0, 0.0)
+        for l, h in zip(w.lo, w.hi):
+            z *= (complex(math.cos(h), math.sin(h)) - complex(math.cos(l), math.sin(l))) / 1j
+        return z.imag
+    raise ValueError("no closed form for " + w.integrand)
+
+
+def median_first(firsts):
+    """Median over seeds of the first n meeting a criterion (unmet = never):
+    (n, seed) of the median seed, or (None, None) when fewer than half met it."""
+    order = sorted(range(len(firsts)), key=lambda i: (firsts[i] is None, firsts[i] or 0, i))
+    mid = order[len(order) // 2]
+    return (firsts[mid], mid) if firsts[mid] is not None else (None, None)
+
+
+def run_tta(zmc, stream):
+    """Time to a relative error of 1e-4 on the 9-D normalised Gaussian
+    (sigma 0.1 on [-1,1]^9, k = 3, 8 trials, depth 4, m = 2) at n = 2^10,
+    2^11, ... points per cell and trial.  Two criteria per seed: the error
+    against the closed form, |value - exact| / |exact| <= 1e-4, and the
+    stated error, 3 std / |value| <= 1e-4; each is the median over five seeds
+    of the first n that meets it.  The five seeds run as one batched call per
+    n (a batched result equals the single run bit for bit).  At the median
+    seed's n, a single FP32-mixed run and an FP64 run are timed; the FP64
+    stream draws other points, so its error at that n is an independent draw
+    of the same estimator's error and is reported beside its time.  Every time
+    is host wall clock around the first call on a fresh handle: parameters up,
+    buffers, graph capture, all levels and the result down."""
+    import torch
+    from paper_1902_07916_gb300 import workloads
+    w = workloads.gauss9d()
+    exact = exact_value(w)
+    crit = {"rel_err": lambda r: abs(r.value - exact) / abs(exact),
+            "three_std": lambda r: 3.0 * r.std / abs(r.value) if r.value else math.inf}
+    first = {c: [None] * TTA_SEEDS for c in crit}
+    batch_s, sweep = {}, []
+
+    def handle(n, seed, prec):
+        h = zmc.zmc_create(w.dim, w.lo, w.hi, w.k, n, w.trials, w.depth, w.sigma_multiplier,
+                           seed)
+        zmc.zmc_set_integrand(h, w.integrand, w.params)
+        zmc.zmc_set_precision(h, prec)
+        return h
+
+    def timed_single(n, seed, prec):
+        h = handle(n, seed, prec)
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = zmc.zmc_integrate(h, stream)
+            return time.perf_counter() - t0, r
+        finally:
+            zmc.zmc_destroy(h)
+
+    # untimed: load the kernels and fill the launch-shape tuner's cache
+    for prec in (zmc.ZMC_FP32_FP64ACC, zmc.ZMC_FP64):
+        timed_single(TTA_N[0], 0, prec)
+
+    t_start = time.perf_counter()
+    for n in TTA_N:
+        hs = [handle(n, s, zmc.ZMC_FP32_FP64ACC) for s in range(TTA_SEEDS)]
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = zmc.zmc_integrate_batch(hs, stream)
+            batch_s[n] = time.perf_counter() - t0
+        finally:
+            for h in hs:
+                zmc.zmc_destroy(h)
+        row = {"n": n, "batch_call_s": round(batch_s[n], 4), "samples_seed0": res[0].samples}
+        for c, f in crit.items():
+            errs = [f(r) for r in res]
+            row[c] = [float("%.3g" % e) for e in errs]
+            for i, e in enumerate(errs):
+                if first[c][i] is None and e <= TTA_TARGET:
+                    first[c][i] = n
+        sweep.append(row)
+        if all(x is not None for c in crit for x in first[c]):
+            break
+        if time.perf_counter() - t_start > TTA_SWEEP_BUDGET_S:
+            break
+
+    out = {"workload": "gauss9d: normalised Gaussian sigma=0.1 on [-1,1]^9, k=3, trials=8, "
+                       "depth=4, m=2, default budget; n doubled from 2^10",
+           "target": TTA_TARGET, "seeds": TTA_SEEDS, "exact": exact,
+           "timing": "host wall clock, first zmc_integrate(_batch) call on fresh handles",
+           "sweep": sweep}
+    for c in crit:
+        n_med, seed = median_first(first[c])
+        entry = {"first_n_per_seed": first[c], "median_n": n_med}
+        if n_med is not None:
+            t32, r32 = timed_single(n_med, seed, zmc.ZMC_FP32_FP64ACC)
+            entry.update({"seed": seed, "fp32_mixed_s": round(t32, 4),
+                          "batched_s_per_integral": round(batch_s[n_med] / TTA_SEEDS, 4),
+                          "batched_call_s": round(batch_s[n_med], 4),
+                          "fp32_mixed_err": float("%.3g" % crit[c](r32))})
+            if t32 * 14 <= TTA_FP64_BUDGET_S:
+                t64, r64 = timed_single(n_med, seed, zmc.ZMC_FP64)
+                entry.update({"fp64_s": round(t64, 4),
+                              "fp64_err": float("%.3g" % crit[c](r64)),
+                              "fp64_over_fp32_mixed": round(t64 / t32, 2)})
+            else:
+                entry["fp64_s"] = None
+                entry["fp64_note"] = "not run: estimated over %.0f s" % TTA_FP64_BUDGET_S
+        out[c] = entry
+    return out
 
 
 # ------------------------------------------------------ CPU baseline
@@ -469,12 +601,11 @@ def run_paper(args):
     from paper_1902_07916_gb300 import build as libbuild
     libbuild.build()
     from paper_1902_07916_gb300 import zmc
-    from oracle import closed_forms
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     rows = []
     for label, table, w in paper_runs():
-        exact = closed_forms.integral(w.integrand, w.lo, w.hi, w.params)
+        exact = exact_value(w)
         for prec in ("fp64", "fp32_fp64acc"):
             with zmc.Integrator(w.dim, w.lo, w.hi, w.k, w.n, w.trials, w.depth,
                                 w.sigma_multiplier, w.seed, w.integrand, w.params,

@@ -310,6 +310,14 @@ double trig_argument_bound(const zmc_ctx* h) {
     return b;
 }
 
+const void* batch_kernel(int mode, int fn, bool wide) {
+    switch (mode) {
+    case ZMC_FP64: return batch_kernel_fp64(fn, wide);
+    case ZMC_FP32_FP64ACC: return batch_kernel_fp32_fp64acc(fn, wide);
+    default: return batch_kernel_fp32_kahan(fn, wide);
+    }
+}
+
 const void* eval_kernel(const zmc_ctx* h) {
     if (h->integrand == kExpression) return h->jit.kernel;
     // 8192 is the FP32 reduction's limit; the margin covers FP32 rounding of
@@ -539,11 +547,20 @@ int finish_result(zmc_ctx* h, zmc_result* out) {
 
 // Device tables and per-level graphs of the last batch, reused while the
 // same handles (same buffers, precision and depth) come back.
+// Integrals of a batch that share a sampling kernel (integrand and trig
+// variant): a contiguous range of the device table.
+struct BatchGroup {
+    const void* kernel;
+    int start, count, grid;
+};
+constexpr int kMaxBatchGroups = 2 * kNumIntegrands;
+
 struct BatchCache {
     int device = -1, capacity = 0;
     int count = 0, mode = -1, depth = 0;
     std::vector<Buffers> sel;
     std::vector<BatchEval> eval;
+    std::vector<BatchGroup> groups;
     Desc* d_desc = nullptr;
     Desc* h_desc = nullptr;            // pinned
     Buffers* d_sel = nullptr;
@@ -554,6 +571,8 @@ struct BatchCache {
     zmc_result* d_out = nullptr;
     zmc_result* h_out = nullptr;       // pinned
     cudaStream_t cap = nullptr;
+    cudaStream_t side[kMaxBatchGroups] = {};     // branches of a level's graph
+    cudaEvent_t fork = nullptr, join[kMaxBatchGroups] = {};
     std::vector<cudaGraphExec_t> graphs;
 
     void drop_graphs() {
@@ -569,6 +588,11 @@ struct BatchCache {
         if (h_desc) cudaFreeHost(h_desc);
         if (h_out) cudaFreeHost(h_out);
         if (cap) cudaStreamDestroy(cap);
+        for (int g = 0; g < kMaxBatchGroups; ++g) {
+            if (side[g]) cudaStreamDestroy(side[g]);
+            if (join[g]) cudaEventDestroy(join[g]);
+        }
+        if (fork) cudaEventDestroy(fork);
         *this = BatchCache{};
     }
     int reserve(int n, int dev) {
@@ -580,11 +604,16 @@ struct BatchCache {
         if (e == cudaSuccess) e = cudaMalloc(&d_sel, sizeof(Buffers) * n);
         if (e == cudaSuccess) e = cudaMalloc(&d_eval, sizeof(BatchEval) * n);
         if (e == cudaSuccess) e = cudaMalloc(&d_l1, sizeof(int64_t) * n);
-        if (e == cudaSuccess) e = cudaMalloc(&d_offsets, sizeof(int64_t) * (n + 1));
-        if (e == cudaSuccess) e = cudaMalloc(&d_head, sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc(&d_offsets, sizeof(int64_t) * (n + kMaxBatchGroups));
+        if (e == cudaSuccess) e = cudaMalloc(&d_head, sizeof(unsigned long long) * kMaxBatchGroups);
         if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(zmc_result) * n);
         if (e == cudaSuccess) e = cudaMallocHost(&h_out, sizeof(zmc_result) * n);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        for (int g = 0; e == cudaSuccess && g < kMaxBatchGroups; ++g) {
+            e = cudaStreamCreateWithFlags(&side[g], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[g], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
         if (e != cudaSuccess) {
             release();
             return cuda_fail(nullptr, e, "batch tables");
@@ -882,10 +911,12 @@ ZMC_API int zmc_integrate_batch(int count, const zmc_handle* hs, void* stream,
     }
     int rc = B.reserve(count, dev);
     if (rc != ZMC_OK) return rc;
-    // what the kernels are told about each integral
+    // what the kernels are told about each integral; the sampling table is
+    // ordered by kernel so that each group is a contiguous range
     std::vector<Buffers> sel(count);
     std::vector<BatchEval> ev(count);
     std::vector<int64_t> l1(count);
+    std::vector<const void*> kern(count);
     for (int i = 0; i < count; ++i) {
         zmc_ctx* h = hs[i];
         sel[i] = h->buf;
@@ -898,9 +929,24 @@ ZMC_API int zmc_integrate_batch(int count, const zmc_handle* hs, void* stream,
         ev[i].keys = philox_keys(h->seed);
         ev[i].fn = h->integrand;
         ev[i].wide = trig_argument_bound(h) > 0.99 * 8192.0 ? 1 : 0;
+        kern[i] = batch_kernel(mode, ev[i].fn, ev[i].wide != 0);
         l1[i] = ipow_sat(h->k, h->dim, INT64_MAX);
         build_desc(h, B.h_desc[i]);
     }
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return std::make_pair(ev[a].fn, ev[a].wide) < std::make_pair(ev[b].fn, ev[b].wide);
+    });
+    std::vector<BatchEval> ev_sorted(count);
+    std::vector<BatchGroup> groups;
+    for (int r = 0; r < count; ++r) {
+        ev_sorted[r] = ev[order[r]];
+        if (groups.empty() || groups.back().kernel != kern[order[r]])
+            groups.push_back(BatchGroup{kern[order[r]], r, 0, 0});
+        ++groups.back().count;
+    }
+    ev.swap(ev_sorted);
     cudaStream_t s = (cudaStream_t)stream;
     const bool same = B.count == count && B.mode == mode && B.depth == depth &&
                       !B.graphs.empty() &&
@@ -919,19 +965,33 @@ ZMC_API int zmc_integrate_batch(int count, const zmc_handle* hs, void* stream,
         B.count = count;
         B.mode = mode;
         B.depth = depth;
-        int per_sm = 0, sms = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_eval_kernel(mode),
-                                                      kBatchThreads, 0);
+        int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int grid = std::max(1, per_sm) * std::max(1, sms);
+        for (BatchGroup& g : groups) {
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, g.kernel, kBatchThreads, 0);
+            g.grid = std::max(1, per_sm) * std::max(1, sms);
+        }
+        B.groups = groups;
         for (int L = 1; L <= depth; ++L) {
             cudaGraph_t g = nullptr;
             e = cudaStreamBeginCapture(B.cap, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch capture");
             cudaError_t le = cudaSuccess;
             if (L == 1) le = launch_init_batch(B.d_sel, B.d_l1, count, B.cap);
-            if (le == cudaSuccess)
-                le = launch_batch_level(B.d_eval, count, L, B.d_offsets, B.d_head, mode, grid, B.cap);
+            // one branch per group: its plan and sampling kernels
+            if (le == cudaSuccess && groups.size() > 1) le = cudaEventRecord(B.fork, B.cap);
+            for (size_t j = 0; le == cudaSuccess && j < groups.size(); ++j) {
+                const BatchGroup& G = groups[j];
+                cudaStream_t bs = j == 0 ? B.cap : B.side[j];
+                if (j > 0) le = cudaStreamWaitEvent(bs, B.fork, 0);
+                if (le == cudaSuccess)
+                    le = launch_batch_level(B.d_eval + G.start, G.count, L,
+                                            B.d_offsets + G.start + j, B.d_head + j, G.kernel,
+                                            G.grid, bs);
+                if (le == cudaSuccess && j > 0) le = cudaEventRecord(B.join[j], bs);
+                if (le == cudaSuccess && j > 0) le = cudaStreamWaitEvent(B.cap, B.join[j], 0);
+            }
             if (le == cudaSuccess) le = launch_select_batch(B.d_sel, count, L, B.cap);
             if (le == cudaSuccess && L == depth) le = launch_final_batch(B.d_sel, B.d_out, count, B.cap);
             e = cudaStreamEndCapture(B.cap, &g);

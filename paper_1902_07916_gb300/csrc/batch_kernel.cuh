@@ -1,0 +1,104 @@
+// Batched sampling kernel (kernel (a) over many integrals).  One persistent
+// kernel per (integrand, trig-variant) group of a batch: its warps pop work
+// units of the group's integrals from an atomic queue, find the unit's
+// integral by binary search in the group's prefix sums and run the unit
+// exactly as the single-integral kernel would (same unit decomposition, same
+// sample loop compiled for the integral's dimension, same order of
+// summation, partial sums written to the integral's own slots), so every
+// integral's result equals its single-integral result bit for bit.
+#pragma once
+
+#include "eval_kernel.cuh"
+#include "zmc_internal.h"
+
+namespace zmc {
+
+// CTAs per SM the batched kernel's register allocation must allow.  In the
+// FP32 modes one fewer than the single kernel: an integral's Philox round
+// keys are loaded into registers per unit (the single kernel takes them from
+// the constant bank as kernel parameters).
+template <int MODE>
+constexpr int batch_min_blocks() { return MODE == ZMC_FP64 ? eval_min_blocks<MODE>() : 3; }
+static_assert(kBatchThreads == kEvalMaxThreads, "shared slices are sized for kEvalMaxThreads");
+
+template <int MODE, int FN, bool WIDE>
+__global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<MODE>())
+zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
+               const int64_t* __restrict__ offsets, unsigned long long* head) {
+    using R = typename ModeTraits<MODE>::R;
+    using R2 = typename ModeTraits<MODE>::R2;
+    __shared__ R2 s_coef[kEvalMaxWarps][ZMC_MAX_DIM];
+    __shared__ double s_term[kEvalMaxWarps][ZMC_MAX_DIM];
+    __shared__ R s_pb[kEvalMaxWarps][ZMC_MAX_DIM];
+    __shared__ R s_c[kEvalMaxWarps][4];
+    __shared__ double2 s_acc[MODE == ZMC_FP32_FP64ACC ? kBatchThreads : 1];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t total = offsets[count];
+    double2* slot = &s_acc[MODE == ZMC_FP32_FP64ACC ? tid : 0];
+    R2* wc = s_coef[warp];
+    double* wt = s_term[warp];
+    R* wp = s_pb[warp];
+    R* wcst = s_c[warp];
+    for (;;) {
+        unsigned long long mine = 0ull;
+        if (lane == 0) mine = atomicAdd(head, 1ull);
+        const int64_t u = (int64_t)__shfl_sync(0xFFFFFFFFu, mine, 0);
+        if (u >= total) break;
+        int lo = 0, hi = count;          // the integral i with offsets[i] <= u < offsets[i+1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (offsets[mid] <= u) lo = mid;
+            else hi = mid;
+        }
+        const BatchEval& it = items[lo];
+        const Desc& D = *it.desc;
+        const UnitPlan plan = unit_plan<MODE>(D, it.st->cells[level]);
+        const int64_t local = u - offsets[lo];
+        const Unit un = unit_of(plan, local);
+        if (lane < D.d) wp[lane] = (R)D.pb[lane];
+        if (lane < 4) wcst[lane] = (R)D.c[lane];
+        const PhiloxKeys keys = it.keys;
+        const R start = fold_setup<MODE, FN>(D, level, un.q, it.parents[level & 1], wc, wt);
+        const StreamConst sc = stream_const(keys, un.t, (uint32_t)un.q, (uint32_t)level);
+        LaneSums<MODE> acc(slot);
+#define ZMC_BATCH_CASE(DD)                                                                    \
+    case DD:                                                                                  \
+        sample_unit_fold<MODE, FN, WIDE, DD>(acc, keys, sc, wc, wp, wcst, start, un.g0, un.g1, \
+                                             plan.ngroups - 1, plan.tail);                     \
+        break;
+        switch (D.d) {
+            ZMC_BATCH_CASE(1) ZMC_BATCH_CASE(2) ZMC_BATCH_CASE(3) ZMC_BATCH_CASE(4)
+            ZMC_BATCH_CASE(5) ZMC_BATCH_CASE(6) ZMC_BATCH_CASE(7) ZMC_BATCH_CASE(8)
+            ZMC_BATCH_CASE(9) ZMC_BATCH_CASE(10) ZMC_BATCH_CASE(11) ZMC_BATCH_CASE(12)
+            ZMC_BATCH_CASE(13) ZMC_BATCH_CASE(14) ZMC_BATCH_CASE(15) ZMC_BATCH_CASE(16)
+            default: break;
+        }
+#undef ZMC_BATCH_CASE
+        acc.reduce_store(it.sums + local);
+        __syncwarp();   // the warp's shared slices are rewritten by its next unit
+    }
+}
+
+// One mode's batched instantiations, indexed like eval_kernel_for().
+template <int MODE>
+inline const void* batch_kernel_for(int fn, bool wide) {
+    const bool w = wide && MODE != ZMC_FP64;
+    switch (fn) {
+    case kConstant: return (const void*)zmc_batch_eval<MODE, kConstant, false>;
+    case kLinear: return (const void*)zmc_batch_eval<MODE, kLinear, false>;
+    case kSinSum:
+        return w ? (const void*)zmc_batch_eval<MODE, kSinSum, true>
+                 : (const void*)zmc_batch_eval<MODE, kSinSum, false>;
+    case kGaussNorm: return (const void*)zmc_batch_eval<MODE, kGaussNorm, false>;
+    case kGenzOsc:
+        return w ? (const void*)zmc_batch_eval<MODE, kGenzOsc, true>
+                 : (const void*)zmc_batch_eval<MODE, kGenzOsc, false>;
+    case kGenzProdPeak: return (const void*)zmc_batch_eval<MODE, kGenzProdPeak, false>;
+    case kGenzGauss: return (const void*)zmc_batch_eval<MODE, kGenzGauss, false>;
+    case kGenzCorner: return (const void*)zmc_batch_eval<MODE, kGenzCorner, false>;
+    default: return nullptr;
+    }
+}
+
+}  // namespace zmc

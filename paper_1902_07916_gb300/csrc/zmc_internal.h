@@ -73,9 +73,15 @@ struct BatchEval {
 // Batched form (batch.cu, select.cu): `items` / `level1_cells` / `out` are
 // device arrays of `count` entries; row y of each selection grid works on
 // integral y.
-const void* batch_eval_kernel(int mode);
+// Batched sampling kernels of one mode by integrand (eval_fp*.cu).
+const void* batch_kernel_fp64(int fn, bool wide);
+const void* batch_kernel_fp32_fp64acc(int fn, bool wide);
+const void* batch_kernel_fp32_kahan(int fn, bool wide);
+// Plan + sampling kernel of one group of `count` integrals (same integrand):
+// `offsets` has count + 1 entries, `head` is the group's queue counter.
 cudaError_t launch_batch_level(const BatchEval* items, int count, int level, int64_t* offsets,
-                               unsigned long long* head, int mode, int grid, cudaStream_t s);
+                               unsigned long long* head, const void* kernel, int grid,
+                               cudaStream_t s);
 cudaError_t launch_init_batch(const Buffers* items, const int64_t* level1_cells, int count,
                               cudaStream_t s);
 cudaError_t launch_select_batch(const Buffers* items, int count, int level, cudaStream_t s);

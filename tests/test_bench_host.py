@@ -1,0 +1,32 @@
+"""Host-side logic of the benchmark: the closed forms it times accuracy
+against, and the median-over-seeds rule of the time-to-accuracy leg."""
+import math
+
+import pytest
+
+import bench
+from oracle import closed_forms as CF
+from paper_1902_07916_gb300 import workloads
+
+
+@pytest.mark.parametrize("make", [workloads.sin3d, workloads.sin6d, workloads.gauss9d,
+                                  lambda: workloads.gauss9d(0.3)])
+def test_exact_value_matches_oracle_closed_forms(make):
+    w = make()
+    assert math.isclose(bench.exact_value(w), CF.integral(w.integrand, w.lo, w.hi, w.params),
+                        rel_tol=1e-13, abs_tol=1e-15)
+
+
+def test_exact_value_textbook_numbers():
+    # Im((e^{10i} - 1)/i)^3 and ^6, evaluated independently of either implementation
+    z = (complex(math.cos(10.0), math.sin(10.0)) - 1.0) / 1j
+    assert math.isclose(bench.exact_value(workloads.sin3d()), (z ** 3).imag, rel_tol=1e-14)
+    assert math.isclose(bench.exact_value(workloads.sin6d()), -49.16507381641946, rel_tol=1e-13)
+    assert math.isclose(bench.exact_value(workloads.gauss9d()), math.erf(1 / (0.1 * 2 ** 0.5)) ** 9)
+
+
+def test_median_first():
+    assert bench.median_first([4, 2, 8, 1, 16]) == (4, 0)
+    assert bench.median_first([None, 2, None, 1, 16]) == (16, 4)
+    assert bench.median_first([None, 2, None, 1, None]) == (None, None)
+    assert bench.median_first([2, 2, 2, 2, 2]) == (2, 2)
