@@ -177,6 +177,57 @@ def philox_multiplies_per_sample(d: int, fp64: bool) -> float:
     return d / (4.0 if fp64 else 5.0) * 17
 
 
+def algorithmic_bytes_per_launch(cells_per_level, n, trials, fp64):
+    """Bytes the sampling kernel must move per launch, averaged over the
+    step's levels: one (S1, S2) pair of doubles written per work unit (a
+    (cell, trial) tile is cut into `chunks` units so that a level has at
+    least 2^18 of them, each of at least 1024 point groups); its reads (the
+    parameters, 2.9 KB, and the parent list, 4 d bytes per flagged cell) are
+    below 0.01% of that and left out."""
+    group = 4 if fp64 else 5
+    ngroups = -(-n // group)
+    total, launches = 0, 0
+    for cells in cells_per_level:
+        if cells <= 0:
+            continue
+        tiles = cells * trials
+        want = -(-(1 << 18) // tiles)
+        most = max(1, ngroups // 1024)
+        chunks = max(1, want) if want < most else most
+        total += 16 * tiles * chunks
+        launches += 1
+    return total / max(launches, 1)
+
+
+# DRAM bytes of the sampling kernel per launch on this benchmark's step (sin6d,
+# FP32-mixed; levels 1 and 2), from one ncu capture of the metrics
+# dram__bytes_read.sum and dram__bytes_write.sum, and the SHA-256 of the
+# kernel's sources it was taken on (profiles/zmc_eval_reduce_sin6d_traffic.md).
+TRAFFIC_CAPTURE = {
+    "workload": "sin6d", "fp64": False,
+    "bytes_per_launch": (73216 + 0 + 11310336 + 173880576) / 2,
+    "sources_sha256": "0e4aa08d4f8ebf8c04003753d9a72cfd092ddbc6d4cf2d56d7d36def9fe55538",
+}
+KERNEL_SOURCES = ["eval_kernel.cuh", "zmc_device.cuh", "zmc_layout.h", "eval_fp32.cu"]
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1902_07916_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def traffic_per_launch(w, fp64):
+    c = TRAFFIC_CAPTURE
+    if w.name != c["workload"] or fp64 != c["fp64"] or kernel_sources_sha256() != c[
+            "sources_sha256"]:
+        return None
+    return round(c["bytes_per_launch"])
+
+
 # Wide (32x32->64-bit) integer multiplies per SM per clock on this GPU: the
 # IMAD.WIDE issue rate (half the 64-lane IMAD rate), which bounds the
 # sampling kernel; a Philox-only loop measures 1.49 blocks/clk/SM = 29.8.
@@ -203,7 +254,6 @@ def run_ours(args, world, rank, local):
     for _ in range(max(args.warmup, 0)):
         it.enqueue(stream)
     torch.cuda.synchronize(dev)
-    kernels_per_run, h2d_bytes, d2h_bytes = zmc.zmc_run_info(it.h)
 
     step_ms, eval_ms, samples, results = [], [], [], []
     barrier(world)
@@ -226,6 +276,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize(dev)
     barrier(world)
     clk = clocks.summary()
+    kernels_per_run, h2d_bytes, d2h_bytes = zmc.zmc_run_info(it.h)
 
     total_ms = sum(step_ms)
     t_max, all_samples, value = weak_scaling_value(world, total_ms, float(sum(samples)))
@@ -254,7 +305,13 @@ def run_ours(args, world, rank, local):
         it64 = zmc.Integrator(w.dim, w.lo, w.hi, w.k, w.n, w.trials, w.depth,
                               w.sigma_multiplier, seed, w.integrand, w.params,
                               precision=zmc.ZMC_FP64)
-        it64.enqueue(stream)                      # warm-up (graph capture)
+        # warm-up on level 1 alone (same kernel: loads it and fills the
+        # launch-shape tuner's cache), then one timed run of the whole tree
+        # (its graph is captured on the host before the launch, which adds
+        # milliseconds at most)
+        with zmc.Integrator(w.dim, w.lo, w.hi, w.k, w.n, w.trials, 1, w.sigma_multiplier,
+                            seed, w.integrand, w.params, precision=zmc.ZMC_FP64) as warm:
+            warm.integrate(stream)
         torch.cuda.synchronize(dev)
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -267,7 +324,7 @@ def run_ours(args, world, rank, local):
         it64.close()
         ref = results[-1]
         fp64 = {"value": r64.samples / (ms64 * 1e-3) / 1e9, "unit": UNIT, "steps": 1,
-                "warmup": 1, "speedup_of_headline": value / (r64.samples / (ms64 * 1e-3) / 1e9),
+                "warmup": "one level-1 run", "speedup_of_headline": value / (r64.samples / (ms64 * 1e-3) / 1e9),
                 "result": r64.value, "std": r64.std,
                 "headline_minus_fp64_over_std": (ref.value - r64.value) / r64.std
                 if r64.std > 0 else None,
@@ -316,7 +373,12 @@ def run_ours(args, world, rank, local):
             "work_per_sample": philox_multiplies_per_sample(w.dim, prec == zmc.ZMC_FP64),
             "kernel_ms_per_step": round(sum(eval_ms) / len(eval_ms), 3),
             "kernel_share_of_step": round(sum(eval_ms) / total_ms, 4),
-            "traffic": None,
+            "algorithmic_bytes": round(algorithmic_bytes_per_launch(
+                r.cells_per_level, w.n, w.trials, prec == zmc.ZMC_FP64)),
+            "traffic": traffic_per_launch(w, prec == zmc.ZMC_FP64),
+            "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
+                             "mean over one step's launches; null unless the kernel sources "
+                             "match the capture",
         },
         "clocks": clk,
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
@@ -489,6 +551,7 @@ def run_tta(zmc, stream):
                 t64, r64 = timed_single(n_med, seed, zmc.ZMC_FP64)
                 entry.update({"fp64_s": round(t64, 4),
                               "fp64_err": float("%.3g" % crit[c](r64)),
+                              "fp64_met_target": crit[c](r64) <= TTA_TARGET,
                               "fp64_over_fp32_mixed": round(t64 / t32, 2)})
             else:
                 entry["fp64_s"] = None
