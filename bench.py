@@ -177,6 +177,21 @@ def philox_multiplies_per_sample(d: int, fp64: bool) -> float:
     return d / (4.0 if fp64 else 5.0) * 17
 
 
+def fp32_flops_per_sample(integrand: str, d: int) -> int:
+    """Counted FP32 flops per point of the FP32 modes (an FMA is 2, a multiply
+    or add 1; the one hardware sine/cosine/exp2/reciprocal per point is an XU
+    op, not a flop): the fold over the dimensions, the finishing function with
+    its range reduction (a multiply and two FMAs for sine and cosine), and the
+    reduction (S1 += f, S2 = fma(f, f, S2): 3)."""
+    if integrand == "genz_corner":
+        e = d + 1
+        return 2 * d + e.bit_length() + bin(e).count("1") + 3
+    per = {"constant": 3, "linear": 2 * d + 4, "sin_sum": 2 * d + 8,
+           "gauss_norm": 4 * d + 6, "genz_osc": 2 * d + 9, "genz_prodpeak": 5 * d + 3,
+           "genz_gauss": 4 * d + 4}
+    return per[integrand]
+
+
 def algorithmic_bytes_per_launch(cells_per_level, n, trials, fp64):
     """Bytes the sampling kernel must move per launch, averaged over the
     step's levels: one (S1, S2) pair of doubles written per work unit (a
@@ -373,6 +388,11 @@ def run_ours(args, world, rank, local):
             "work_per_sample": philox_multiplies_per_sample(w.dim, prec == zmc.ZMC_FP64),
             "kernel_ms_per_step": round(sum(eval_ms) / len(eval_ms), 3),
             "kernel_share_of_step": round(sum(eval_ms) / total_ms, 4),
+            "fp32_flops_per_sample": None if prec == zmc.ZMC_FP64 else fp32_flops_per_sample(
+                w.integrand, w.dim),
+            "fp32_flop_frac": None if prec == zmc.ZMC_FP64 else round(
+                fp32_flops_per_sample(w.integrand, w.dim) * sum(samples) / eval_s
+                / (2 * 128 * sms * max_mhz * 1e6), 4),
             "algorithmic_bytes": round(algorithmic_bytes_per_launch(
                 r.cells_per_level, w.n, w.trials, prec == zmc.ZMC_FP64)),
             "traffic": traffic_per_launch(w, prec == zmc.ZMC_FP64),
