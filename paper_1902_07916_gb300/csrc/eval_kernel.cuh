@@ -184,6 +184,28 @@ __device__ __forceinline__ UnitPlan unit_plan(const Desc& D, int64_t C) {
     return p;
 }
 
+// Distribution of a level's units over the warps of the sampling kernel:
+// a warp's first unit is its global warp index, every further one comes
+// from the level's counter in the tree state (one atomic per unit of >= 1024
+// point groups).  A unit's sums do not depend on which warp runs it, so the
+// results are the same under any order; the queue keeps every warp busy up
+// to the level's last unit, where a fixed stride leaves the warps that the
+// schedulers favoured idle at the end.
+struct UnitQueue {
+    unsigned long long* head;
+    int64_t nwarps;
+    __device__ __forceinline__ UnitQueue(State* st, int level)
+        : head(&st->queue[level]), nwarps((int64_t)gridDim.x * (blockDim.x >> 5)) {}
+    __device__ __forceinline__ int64_t first() const {
+        return (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    }
+    __device__ __forceinline__ int64_t next() const {
+        unsigned long long mine = 0ull;
+        if ((threadIdx.x & 31) == 0) mine = atomicAdd(head, 1ull);
+        return nwarps + (int64_t)__shfl_sync(0xFFFFFFFFu, mine, 0);
+    }
+};
+
 // Unit u -> (slot q, trial t, group range [g0, g1)).
 struct Unit {
     int64_t q;
@@ -284,7 +306,7 @@ __device__ __forceinline__ void sample_unit_fold(
 
 template <int MODE, int FN, bool WIDE>
 __global__ void __launch_bounds__(kEvalMaxThreads, eval_min_blocks<MODE>())
-zmc_eval_reduce(const Desc* __restrict__ desc, const State* __restrict__ st,
+zmc_eval_reduce(const Desc* __restrict__ desc, State* st,
                 const uint32_t* __restrict__ parents, double2* __restrict__ partial,
                 int level, const PhiloxKeys keys) {
     using R = typename ModeTraits<MODE>::R;
@@ -304,9 +326,9 @@ zmc_eval_reduce(const Desc* __restrict__ desc, const State* __restrict__ st,
     __syncthreads();
 
     const UnitPlan plan = unit_plan<MODE>(D, C);
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const UnitQueue queue(st, level);
     double2* slot = &s_acc[MODE == ZMC_FP32_FP64ACC ? tid : 0];
-    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; u < plan.units; u += nwarps) {
+    for (int64_t u = queue.first(); u < plan.units; u = queue.next()) {
         const Unit un = unit_of(plan, u);
         const R start = fold_setup<MODE, FN>(D, level, un.q, parents, s_coef[warp], s_term[warp]);
         const StreamConst sc = stream_const(keys, un.t, (uint32_t)un.q, (uint32_t)level);
@@ -333,7 +355,7 @@ zmc_eval_reduce(const Desc* __restrict__ desc, const State* __restrict__ st,
 // at compile time: E::eval(x, p) reads x[0..DIM-1] and the parameters p[].
 template <int MODE, int DIM, class E>
 __device__ __forceinline__ void eval_expr_body(const Desc* __restrict__ desc,
-                                               const State* __restrict__ st,
+                                               State* st,
                                                const uint32_t* __restrict__ parents,
                                                double2* __restrict__ partial, int level,
                                                const PhiloxKeys& keys) {
@@ -355,11 +377,11 @@ __device__ __forceinline__ void eval_expr_body(const Desc* __restrict__ desc,
     __syncthreads();
 
     const UnitPlan plan = unit_plan<MODE>(D, C);
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const UnitQueue queue(st, level);
     double2* slot = &s_acc[MODE == ZMC_FP32_FP64ACC ? tid : 0];
     R2* wb = s_wb[warp];
     constexpr int G = kGroup<MODE>;
-    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; u < plan.units; u += nwarps) {
+    for (int64_t u = queue.first(); u < plan.units; u = queue.next()) {
         const Unit un = unit_of(plan, u);
         if (lane < DIM) {
             const double w = D.width[level][lane];

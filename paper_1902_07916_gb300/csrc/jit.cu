@@ -158,7 +158,7 @@ int jit_compile(const char* expr, int dim, int n_params, int mode, JitKernel* ou
         "  static __device__ __forceinline__ R eval(const R* x, const R* p) {\n"
         "    return (R)(" + e + ");\n  }\n};\n"
         "extern \"C\" __global__ void __launch_bounds__(zmc::kEvalMaxThreads, zmc::eval_min_blocks<" + std::to_string(mode) + ">())\n"
-        "zmc_eval_expr(const zmc::Desc* __restrict__ desc, const zmc::State* __restrict__ st,\n"
+        "zmc_eval_expr(const zmc::Desc* __restrict__ desc, zmc::State* st,\n"
         "              const uint32_t* __restrict__ parents, double2* __restrict__ sums, int level,\n"
         "              const zmc::PhiloxKeys keys) {\n"
         "  zmc::eval_expr_body<" + std::to_string(mode) + ", " + std::to_string(dim) +

@@ -86,8 +86,14 @@ __device__ __forceinline__ double one_plus_word_f64(uint32_t w) {
 // 23 f + 22); u = (field + 1/2) 2^-23, exact in binary32.  The float
 // 1 + field 2^-23 is assembled from the bits, and the point is
 // w_L * (1.m) + (lo + c w_L - (1 - 2^-24) w_L).
+// One three-input LOP3, (field & 0x7FFFFF) | exponent, with the exponent
+// held in a register: left to itself the compiler splits it into two
+// instructions (one immediate operand per LOP3), and the integer ALU is one
+// of the sampling kernel's two busiest pipes.
 __device__ __forceinline__ float one_plus_field(uint32_t field23) {
-    return __uint_as_float(0x3F800000u | (field23 & 0x7FFFFFu));
+    uint32_t r;
+    asm("lop3.b32 %0, %1, 0x7FFFFF, %2, 0xEA;" : "=r"(r) : "r"(field23), "r"(0x3F800000u));
+    return __uint_as_float(r);
 }
 __device__ __forceinline__ void fields_1m(uint4 w, float& v0, float& v1, float& v2, float& v3,
                                           float& v4) {

@@ -60,6 +60,7 @@ struct State {
     int32_t status;      // ZMC_OK or a ZMC_ERR_* code
     int32_t levels_run;
     uint32_t ticket[4];  // last-block arrival counters (self-resetting)
+    unsigned long long queue[ZMC_MAX_DEPTH + 2];  // sampling units taken per level
 };
 
 // Work units of the sampling kernel.  A (cell, trial) tile is cut into
