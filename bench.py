@@ -220,8 +220,8 @@ def algorithmic_bytes_per_launch(cells_per_level, n, trials, fp64):
 # kernel's sources it was taken on (profiles/zmc_eval_reduce_sin6d_traffic.md).
 TRAFFIC_CAPTURE = {
     "workload": "sin6d", "fp64": False,
-    "bytes_per_launch": (73216 + 0 + 11310336 + 173880576) / 2,
-    "sources_sha256": "0e4aa08d4f8ebf8c04003753d9a72cfd092ddbc6d4cf2d56d7d36def9fe55538",
+    "bytes_per_launch": (235520 + 0 + 10405888 + 171250432) / 2,
+    "sources_sha256": "7e93858380265d8339f9d1b698307c80cc792672b32dee04d39d76412e22c431",
 }
 KERNEL_SOURCES = ["eval_kernel.cuh", "zmc_device.cuh", "zmc_layout.h", "eval_fp32.cu"]
 
