@@ -259,10 +259,44 @@ __device__ __forceinline__ typename ModeTraits<MODE>::R fold_setup(
     return (R)a0;
 }
 
+// The values of one point group (G points) of a registry integrand: the
+// Philox block of every dimension (round 1's product A * c0 given as P, the
+// 64-bit product for dimension 0), each folded into the G running sums, then
+// the finishing function.
+template <int MODE, int FN, bool WIDE, int DIM>
+__device__ __forceinline__ void group_values(
+    const PhiloxKeys& keys, const StreamConst& sc,
+    const typename ModeTraits<MODE>::R2* w_coef, const typename ModeTraits<MODE>::R* s_pb,
+    const typename ModeTraits<MODE>::R* s_c, typename ModeTraits<MODE>::R start, uint64_t P,
+    int nd, typename ModeTraits<MODE>::R (&f)[kGroup<MODE>]) {
+    using R = typename ModeTraits<MODE>::R;
+    using R2 = typename ModeTraits<MODE>::R2;
+    using F = Fn<FN, R>;
+    constexpr int G = kGroup<MODE>;
+    R a[G];
+#pragma unroll
+    for (int p = 0; p < G; ++p) a[p] = start;
+#pragma unroll kDimUnroll
+    for (int i = 0; i < nd; ++i) {
+        const uint4 w = philox_from_product(keys, sc, (uint32_t)(P >> 32), (uint32_t)P);
+        P += kPhiloxMulA;
+        const R2 ab = w_coef[i];
+        const R pb = s_pb[i];
+        R v[G];
+        block_points<MODE>(w, v);
+#pragma unroll
+        for (int p = 0; p < G; ++p) a[p] = F::fold(a[p], v[p], ab.x, ab.y, pb);
+    }
+#pragma unroll
+    for (int p = 0; p < G; ++p) f[p] = F::template finish<WIDE>(a[p], s_c, nd);
+}
+
 // The sample loop of one unit for a registry integrand, dimension DIM (a
 // compile-time constant, or 0 to take the dimension from dim_rt).
 // Round 1's product A * c0 is carried as a 64-bit running sum: c0 = g*d+i
-// grows by one per dimension and by 32*d per group of this lane.
+// grows by one per dimension and by 32*d per group of this lane.  Only the
+// tile's last group can hold points past n; it is left out of the main loop
+// and run, masked, by the one lane it falls to in the unit that holds it.
 template <int MODE, int FN, bool WIDE, int DIM>
 __device__ __forceinline__ void sample_unit_fold(
     LaneSums<MODE>& acc, const PhiloxKeys& keys, const StreamConst& sc,
@@ -270,36 +304,25 @@ __device__ __forceinline__ void sample_unit_fold(
     const typename ModeTraits<MODE>::R* s_c, typename ModeTraits<MODE>::R start,
     uint32_t g0, uint32_t g1, uint32_t last_group, uint32_t tail, int dim_rt = 0) {
     using R = typename ModeTraits<MODE>::R;
-    using R2 = typename ModeTraits<MODE>::R2;
-    using F = Fn<FN, R>;
     const int nd = DIM > 0 ? DIM : dim_rt;
     const uint64_t step = (uint64_t)kPhiloxMulA * (uint64_t)(32 * nd);
     uint32_t g = g0 + (threadIdx.x & 31);
     uint64_t Pg = (uint64_t)kPhiloxMulA * (uint64_t)(g * nd);
     constexpr int G = kGroup<MODE>;
-    while (g < g1) {
-        for (int j = 0; j < kFlushGroups && g < g1; ++j, g += 32, Pg += step) {
-            R a[G];
-#pragma unroll
-            for (int p = 0; p < G; ++p) a[p] = start;
-            uint64_t P = Pg;
-#pragma unroll kDimUnroll
-            for (int i = 0; i < nd; ++i) {
-                const uint4 w = philox_from_product(keys, sc, (uint32_t)(P >> 32), (uint32_t)P);
-                P += kPhiloxMulA;
-                const R2 ab = w_coef[i];
-                const R pb = s_pb[i];
-                R v[G];
-                block_points<MODE>(w, v);
-#pragma unroll
-                for (int p = 0; p < G; ++p) a[p] = F::fold(a[p], v[p], ab.x, ab.y, pb);
-            }
+    const uint32_t full_end = g1 <= last_group ? g1 : last_group;
+    while (g < full_end) {
+        for (int j = 0; j < kFlushGroups && g < full_end; ++j, g += 32, Pg += step) {
             R f[G];
-#pragma unroll
-            for (int p = 0; p < G; ++p) f[p] = F::template finish<WIDE>(a[p], s_c, nd);
-            mask_tail(g == last_group, tail, f);
+            group_values<MODE, FN, WIDE, DIM>(keys, sc, w_coef, s_pb, s_c, start, Pg, nd, f);
             acc.add(f);
         }
+        acc.flush();
+    }
+    if (g == last_group && g < g1) {
+        R f[G];
+        group_values<MODE, FN, WIDE, DIM>(keys, sc, w_coef, s_pb, s_c, start, Pg, nd, f);
+        mask_tail(true, tail, f);
+        acc.add(f);
         acc.flush();
     }
 }
