@@ -67,10 +67,14 @@ extern "C" {
 /* The FP32 modes draw their points from the FP32 stream (five 23-bit
  * uniforms per Philox block, see zmc_uniforms), so they sample other points
  * than the FP64 mode does: their results differ from it by Monte Carlo
- * noise as well as by rounding.  FP32 flushes integrand values below about
- * 1e-38, so an integrand whose values on the coarse levels are all that
- * small (a Gaussian of width 0.01 in 9-D seen from cells of width 2/3) gives
- * the selection nothing to see: use ZMC_FP64 for it. */
+ * noise as well as by rounding.  The Gaussian integrands ("gauss_norm",
+ * "genz_gauss") are evaluated in the log2 domain in the FP32 modes (each
+ * thread sums 2^(t - k) against its own reference exponent k, and the sums
+ * reach FP64 through ldexp), so values far below FP32's range (1e-38), as a
+ * Gaussian of width 0.01 in 9-D gives on cells of width 2/3, keep their
+ * spread and steer the refinement as in FP64.  Their relative error grows
+ * with the exponent's size and gradient: about 2^-22 (|E| + |grad E| |x|)
+ * for exp(E). */
 
 #define ZMC_MAX_DIM 16
 #define ZMC_MAX_DEPTH 16
@@ -303,6 +307,24 @@ ZMC_API int zmc_run_info(zmc_handle h, int64_t* kernels, int64_t* h2d_bytes,
 ZMC_API int zmc_level_stats_noalloc(const double* sums, int64_t cells, int trials, int64_t n,
                                     double volume, double sigma_multiplier, double* cell_stats,
                                     double* level_stats, void* stream);
+
+/*
+ * zmc_check_expression -- compile an expression integrand (the text after
+ * "expr:" in zmc_set_integrand; Sec. 3.3 names integrands with condition
+ * checks and special functions as a need) for a GPU of compute capability
+ * cc_major.cc_minor with NVRTC, without a device and without loading the
+ * result: a way to validate expressions ahead of time (and what a host
+ * without a GPU can test).
+ *   expr         NUL-terminated expression in x[0..dim-1] and p[...]
+ *   dim          1..16;  mode  ZMC_FP64 | ZMC_FP32_FP64ACC | ZMC_FP32_KAHAN
+ *   log          caller's buffer of log_size bytes (may be NULL when
+ *                log_size is 0): the compiler's log or the reason, truncated
+ *                and NUL-terminated
+ * Errors: ZMC_ERR_ARG (bad sizes or mode, empty expression),
+ * ZMC_ERR_COMPILE (NVRTC rejected it, or libnvrtc could not be opened).
+ */
+ZMC_API int zmc_check_expression(const char* expr, int dim, int mode, int cc_major, int cc_minor,
+                                 char* log, size_t log_size);
 
 /* zmc_last_error -- message of the last failed call on h (or of the last
  * failed zmc_create / handle-less call when h is NULL).  Never NULL; valid

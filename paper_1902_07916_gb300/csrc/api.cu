@@ -137,6 +137,7 @@ void fill_integrand(Desc& D, int id, const std::vector<double>& p) {
         const double s = p[0];
         D.c[0] = -1.0 / (2.0 * s * s);
         D.c[1] = pow(sqrt(2.0 * M_PI) * s, -(double)d);
+        D.c[2] = D.c[0] * M_LOG2E;        // the FP32 modes' log2-domain exponent
         break;
     }
     case kGenzOsc:
@@ -1092,6 +1093,23 @@ ZMC_API int zmc_level_stats_noalloc(const double* sums, int64_t cells, int trial
     const int rc = level_stats_noalloc(sums, cells, trials, n, volume, sigma_multiplier,
                                        cell_stats, level_stats, (cudaStream_t)stream);
     if (rc != ZMC_OK) return fail(nullptr, rc, noalloc_last_error());
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_check_expression(const char* expr, int dim, int mode, int cc_major, int cc_minor,
+                                 char* log, size_t log_size) {
+    if (log && log_size) log[0] = '\0';
+    if (dim < 1 || dim > ZMC_MAX_DIM || cc_major < 1 || cc_minor < 0 || (log_size && !log) ||
+        (mode != ZMC_FP64 && mode != ZMC_FP32_FP64ACC && mode != ZMC_FP32_KAHAN))
+        return fail(nullptr, ZMC_ERR_ARG, "bad arguments");
+    std::string msg;
+    const int rc = jit_check(expr, dim, mode, cc_major, cc_minor, &msg);
+    if (log && log_size) {
+        const size_t m = std::min(msg.size(), log_size - 1);
+        memcpy(log, msg.data(), m);
+        log[m] = '\0';
+    }
+    if (rc != ZMC_OK) return fail(nullptr, rc, msg.c_str());
     return ZMC_OK;
 }
 

@@ -61,7 +61,7 @@ zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
         const PhiloxKeys keys = it.keys;
         const R start = fold_setup<MODE, FN>(D, level, un.q, it.parents[level & 1], wc, wt);
         const StreamConst sc = stream_const(keys, un.t, (uint32_t)un.q, (uint32_t)level);
-        LaneSums<MODE> acc(slot);
+        SumsFor<MODE, FN> acc(slot, value_scale<MODE, FN>(D));
 #define ZMC_BATCH_CASE(DD)                                                                    \
     case DD:                                                                                  \
         sample_unit_fold<MODE, FN, WIDE, DD>(acc, keys, sc, wc, wp, wcst, start, un.g0, un.g1, \

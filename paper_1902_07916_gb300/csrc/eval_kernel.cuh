@@ -86,7 +86,7 @@ struct LaneSums {
     double S1d = 0.0, S2d = 0.0;                   // MODE 0
     double2* slot;                                 // MODE 1
 
-    __device__ __forceinline__ explicit LaneSums(double2* s) : slot(s) {
+    __device__ __forceinline__ explicit LaneSums(double2* s, double = 1.0) : slot(s) {
         if constexpr (MODE == ZMC_FP32_FP64ACC) *slot = make_double2(0.0, 0.0);
     }
 
@@ -154,14 +154,129 @@ struct LaneSums {
     }
 };
 
+// FP32 modes for integrands of the form C * 2^t (the Gaussians): the group
+// delivers t = log2(f / C) and the lane sums 2^(t - k) and 2^(2 (t - k)) in
+// FP32, k an integer reference exponent that follows the largest t the lane
+// has seen (a rebase scales the partial sums by an exact power of two).  The
+// values keep FP32's relative precision whatever their magnitude, so a cell
+// whose values all lie below FP32's range (1e-38) still has a spread, as in
+// FP64.  MODE 1 moves its partials into absolute FP64 sums (ldexp by k, 2k)
+// every kFlushGroups groups; MODE 2 keeps (sum, error) pairs per lane and
+// brings the warp to its largest k before the compensated reduction.  C
+// (FP64) multiplies the unit's sums at the end.
+__device__ __forceinline__ float neg_inf() { return __int_as_float((int)0xff800000u); }
+
+template <int MODE>
+struct LogLaneSums {
+    float k = neg_inf();                          // reference exponent (an integer)
+    float s1 = 0.f, e1 = 0.f, s2 = 0.f, e2 = 0.f;
+    double2* slot;                                // MODE 1
+    double scale;                                 // C
+
+    __device__ __forceinline__ LogLaneSums(double2* s, double c) : slot(s), scale(c) {
+        if constexpr (MODE == ZMC_FP32_FP64ACC) *slot = make_double2(0.0, 0.0);
+    }
+
+    // Scale the partial sums from reference k to kn >= k: 2^(k - kn), exact
+    // (or 0 once below FP32's normal range, where they no longer count).
+    __device__ __forceinline__ void rebase(float kn) {
+        const float d = k - kn;
+        const float sc = d < -126.f ? 0.f : __int_as_float(((int)d + 127) << 23);
+        const float sc2 = d < -63.f ? 0.f : sc * sc;
+        s1 *= sc; e1 *= sc;
+        s2 *= sc2; e2 *= sc2;
+        k = kn;
+    }
+
+    __device__ __forceinline__ void add(const float (&t)[kGroup<MODE>]) {
+        float tm = t[0];
+#pragma unroll
+        for (int j = 1; j < kGroup<MODE>; ++j) tm = fmaxf(tm, t[j]);
+        if (tm > k) rebase(ceilf(tm));
+        float f[kGroup<MODE>];
+#pragma unroll
+        for (int j = 0; j < kGroup<MODE>; ++j) f[j] = exp2f(t[j] - k);
+        const float g1 = ((f[0] + f[1]) + (f[2] + f[3])) + f[4];
+        const float g2 = fmaf(f[4], f[4], fmaf(f[0], f[0], f[1] * f[1]) +
+                                              fmaf(f[2], f[2], f[3] * f[3]));
+        if constexpr (MODE == ZMC_FP32_FP64ACC) {
+            s1 += g1;
+            s2 += g2;
+        } else {
+            float a, r;
+            two_sum(s1, g1, a, r); s1 = a; e1 += r;
+            two_sum(s2, g2, a, r); s2 = a; e2 += r;
+        }
+    }
+
+    // The exponent for ldexp: FP64 sums vanish below 2^-1074, so clamping k
+    // at -4000 changes nothing and keeps the conversion to int in range.
+    static __device__ __forceinline__ int exp_of(float k) { return (int)fmaxf(k, -4000.f); }
+
+    __device__ __forceinline__ void flush() {
+        if constexpr (MODE == ZMC_FP32_FP64ACC) {
+            if (s1 != 0.f || s2 != 0.f) {
+                const int ke = exp_of(k);
+                double2 v = *slot;
+                v.x += ldexp((double)s1, ke);
+                v.y += ldexp((double)s2, 2 * ke);
+                *slot = v;
+            }
+            s1 = 0.f; s2 = 0.f;
+        }
+    }
+
+    __device__ __forceinline__ void reduce_store(double2* out) {
+        double a, b;
+        if constexpr (MODE == ZMC_FP32_FP64ACC) {
+            const double2 v = *slot;
+            a = warp_sum(v.x);
+            b = warp_sum(v.y);
+        } else {
+            float km = k;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) km = fmaxf(km, __shfl_xor_sync(0xFFFFFFFFu, km, o));
+            if (km > k) rebase(km);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const float os1 = __shfl_xor_sync(0xFFFFFFFFu, s1, o);
+                const float oe1 = __shfl_xor_sync(0xFFFFFFFFu, e1, o);
+                const float os2 = __shfl_xor_sync(0xFFFFFFFFu, s2, o);
+                const float oe2 = __shfl_xor_sync(0xFFFFFFFFu, e2, o);
+                float t, r;
+                two_sum(s1, os1, t, r); s1 = t; e1 = e1 + oe1 + r;
+                two_sum(s2, os2, t, r); s2 = t; e2 = e2 + oe2 + r;
+            }
+            const int ke = exp_of(km);
+            a = (km == neg_inf()) ? 0.0 : ldexp((double)s1 + (double)e1, ke);
+            b = (km == neg_inf()) ? 0.0 : ldexp((double)s2 + (double)e2, 2 * ke);
+        }
+        if ((threadIdx.x & 31) == 0) *out = make_double2(a * scale, b * (scale * scale));
+    }
+};
+
+// The lane accumulator of integrand FN in mode MODE.
+template <bool B, class T, class F> struct pick_type { using type = T; };
+template <class T, class F> struct pick_type<false, T, F> { using type = F; };
+template <int MODE, int FN>
+constexpr bool log_domain() { return MODE != ZMC_FP64 && Fn<FN, float>::kLog2; }
+template <int MODE, int FN>
+using SumsFor = typename pick_type<log_domain<MODE, FN>(), LogLaneSums<MODE>, LaneSums<MODE>>::type;
+template <int MODE, int FN>
+__device__ __forceinline__ double value_scale(const Desc& D) {
+    if constexpr (log_domain<MODE, FN>()) return Fn<FN, float>::value_scale(D);
+    else return 1.0;
+}
+
 // Mask the points past n in the tile's last group (only it can be short):
-// `tail` is the number of real points of that group, 1..G.
+// `tail` is the number of real points of that group, 1..G; they become
+// `fill` (0, or -inf for a log2-domain group).
 template <typename R, int G>
-__device__ __forceinline__ void mask_tail(bool last, uint32_t tail, R (&f)[G]) {
+__device__ __forceinline__ void mask_tail(bool last, uint32_t tail, R (&f)[G], R fill = R(0)) {
     if (last) {
 #pragma unroll
         for (int j = 1; j < G; ++j)
-            if ((uint32_t)j >= tail) f[j] = R(0);
+            if ((uint32_t)j >= tail) f[j] = fill;
     }
 }
 
@@ -287,8 +402,13 @@ __device__ __forceinline__ void group_values(
 #pragma unroll
         for (int p = 0; p < G; ++p) a[p] = F::fold(a[p], v[p], ab.x, ab.y, pb);
     }
+    if constexpr (log_domain<MODE, FN>()) {
 #pragma unroll
-    for (int p = 0; p < G; ++p) f[p] = F::template finish<WIDE>(a[p], s_c, nd);
+        for (int p = 0; p < G; ++p) f[p] = F::finish_log2(a[p], s_c);
+    } else {
+#pragma unroll
+        for (int p = 0; p < G; ++p) f[p] = F::template finish<WIDE>(a[p], s_c, nd);
+    }
 }
 
 // The sample loop of one unit for a registry integrand, dimension DIM (a
@@ -299,7 +419,7 @@ __device__ __forceinline__ void group_values(
 // and run, masked, by the one lane it falls to in the unit that holds it.
 template <int MODE, int FN, bool WIDE, int DIM>
 __device__ __forceinline__ void sample_unit_fold(
-    LaneSums<MODE>& acc, const PhiloxKeys& keys, const StreamConst& sc,
+    SumsFor<MODE, FN>& acc, const PhiloxKeys& keys, const StreamConst& sc,
     const typename ModeTraits<MODE>::R2* w_coef, const typename ModeTraits<MODE>::R* s_pb,
     const typename ModeTraits<MODE>::R* s_c, typename ModeTraits<MODE>::R start,
     uint32_t g0, uint32_t g1, uint32_t last_group, uint32_t tail, int dim_rt = 0) {
@@ -321,7 +441,7 @@ __device__ __forceinline__ void sample_unit_fold(
     if (g == last_group && g < g1) {
         R f[G];
         group_values<MODE, FN, WIDE, DIM>(keys, sc, w_coef, s_pb, s_c, start, Pg, nd, f);
-        mask_tail(true, tail, f);
+        mask_tail(true, tail, f, log_domain<MODE, FN>() ? R(neg_inf()) : R(0));
         acc.add(f);
         acc.flush();
     }
@@ -355,7 +475,7 @@ zmc_eval_reduce(const Desc* __restrict__ desc, State* st,
         const Unit un = unit_of(plan, u);
         const R start = fold_setup<MODE, FN>(D, level, un.q, parents, s_coef[warp], s_term[warp]);
         const StreamConst sc = stream_const(keys, un.t, (uint32_t)un.q, (uint32_t)level);
-        LaneSums<MODE> acc(slot);
+        SumsFor<MODE, FN> acc(slot, value_scale<MODE, FN>(D));
 #define ZMC_FOLD_CASE(DD)                                                                      \
     case DD:                                                                                   \
         sample_unit_fold<MODE, FN, WIDE, DD>(acc, keys, sc, s_coef[warp], s_pb, s_c, start,    \

@@ -112,42 +112,35 @@ std::string float_literals(const std::string& e) {
     return out;
 }
 
-}  // namespace
 
-int jit_compile(const char* expr, int dim, int n_params, int mode, JitKernel* out,
-                std::string* log) {
-    std::string e(expr ? expr : "");
-    if (e.empty()) {
+// The expression as pasted into the kernel: one C++ expression, FP32
+// literals in the FP32 modes.  ZMC_OK or ZMC_ERR_ARG / ZMC_ERR_COMPILE.
+int prepare_expression(const char* expr, int mode, std::string* e, std::string* log) {
+    *e = expr ? expr : "";
+    if (e->empty()) {
         *log = "empty expression";
         return ZMC_ERR_ARG;
     }
-    // The expression is pasted into a function body: keep it one expression.
-    for (size_t i = 0; i < e.size(); ++i) {
-        const char c = e[i];
+    for (size_t i = 0; i < e->size(); ++i) {
+        const char c = (*e)[i];
         if (c == ';' || c == '{' || c == '}' || c == '#' || c == '"' || c == '\\' || c == '\'' ||
-            (c == '/' && i + 1 < e.size() && (e[i + 1] == '/' || e[i + 1] == '*'))) {
+            (c == '/' && i + 1 < e->size() && ((*e)[i + 1] == '/' || (*e)[i + 1] == '*'))) {
             *log = "expression may not contain ; { } # quotes, backslashes or comments";
             return ZMC_ERR_COMPILE;
         }
     }
-    if (mode != ZMC_FP64) e = float_literals(e);
-    const std::string key = std::to_string(dim) + "|" + std::to_string(n_params) + "|" +
-                            std::to_string(mode) + "|" + e;
-    std::lock_guard<std::mutex> lock(g_mu);
-    auto it = g_cache.find(key);
-    if (it != g_cache.end()) {
-        out->kernel = it->second;
-        return ZMC_OK;
-    }
+    if (mode != ZMC_FP64) *e = float_literals(*e);
+    return ZMC_OK;
+}
+
+// NVRTC: the sampling kernel with expression `e` for compute capability
+// major.minor, as a cubin.  Needs no device.
+int nvrtc_cubin(const std::string& e, int dim, int mode, int major, int minor,
+                std::vector<char>* cubin, std::string* log) {
     if (!load_nvrtc()) {
         *log = "expression integrands need NVRTC: " + g_nvrtc.why;
         return ZMC_ERR_COMPILE;
     }
-    int dev = 0, major = 0, minor = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-    const char* R = mode == ZMC_FP64 ? "double" : "float";
     std::string src =
         "typedef unsigned int uint32_t;\ntypedef int int32_t;\n"
         "typedef long long int64_t;\ntypedef unsigned long long uint64_t;\n"
@@ -163,7 +156,6 @@ int jit_compile(const char* expr, int dim, int n_params, int mode, JitKernel* ou
         "              const zmc::PhiloxKeys keys) {\n"
         "  zmc::eval_expr_body<" + std::to_string(mode) + ", " + std::to_string(dim) +
         ", ZmcUserExpr>(desc, st, parents, sums, level, keys);\n}\n";
-    (void)R;
     nvrtcProgram prog = nullptr;
     nvrtcResult r = g_nvrtc.create(&prog, src.c_str(), "zmc_expr.cu", kJitNumHeaders, kJitHeaders,
                                    kJitHeaderNames);
@@ -185,9 +177,34 @@ int jit_compile(const char* expr, int dim, int n_params, int mode, JitKernel* ou
     }
     size_t cs = 0;
     g_nvrtc.cubin_size(prog, &cs);
-    std::vector<char> cubin(cs);
-    g_nvrtc.cubin(prog, cubin.data());
+    cubin->assign(cs, 0);
+    g_nvrtc.cubin(prog, cubin->data());
     g_nvrtc.destroy(&prog);
+    return ZMC_OK;
+}
+
+}  // namespace
+
+int jit_compile(const char* expr, int dim, int n_params, int mode, JitKernel* out,
+                std::string* log) {
+    std::string e;
+    int rc = prepare_expression(expr, mode, &e, log);
+    if (rc != ZMC_OK) return rc;
+    const std::string key = std::to_string(dim) + "|" + std::to_string(n_params) + "|" +
+                            std::to_string(mode) + "|" + e;
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+        out->kernel = it->second;
+        return ZMC_OK;
+    }
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    std::vector<char> cubin;
+    rc = nvrtc_cubin(e, dim, mode, major, minor, &cubin, log);
+    if (rc != ZMC_OK) return rc;
     cudaLibrary_t lib = nullptr;
     cudaError_t ce = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (ce != cudaSuccess) {
@@ -203,6 +220,15 @@ int jit_compile(const char* expr, int dim, int n_params, int mode, JitKernel* ou
     g_cache[key] = (const void*)k;
     out->kernel = (const void*)k;
     return ZMC_OK;
+}
+
+int jit_check(const char* expr, int dim, int mode, int major, int minor, std::string* log) {
+    std::string e;
+    int rc = prepare_expression(expr, mode, &e, log);
+    if (rc != ZMC_OK) return rc;
+    std::lock_guard<std::mutex> lock(g_mu);
+    std::vector<char> cubin;
+    return nvrtc_cubin(e, dim, mode, major, minor, &cubin, log);
 }
 
 void jit_release(JitKernel* k) {

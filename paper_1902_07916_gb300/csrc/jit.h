@@ -18,5 +18,8 @@ struct JitKernel {
 int jit_compile(const char* expr, int dim, int n_params, int mode, JitKernel* out,
                 std::string* log);
 void jit_release(JitKernel* k);
+// Compile `expr` for compute capability major.minor without a device (the
+// cubin is dropped).  ZMC_OK or ZMC_ERR_ARG / ZMC_ERR_COMPILE with *log.
+int jit_check(const char* expr, int dim, int mode, int major, int minor, std::string* log);
 
 }  // namespace zmc

@@ -169,12 +169,14 @@ struct Prep {
 };
 
 template <typename R> struct Fn<kConstant, R> {      // c0
+    static constexpr bool kLog2 = false;
     static __device__ __forceinline__ Prep prep(double, double, double, double) { return {0, 0, 0}; }
     static __device__ __forceinline__ R init() { return R(0); }
     static __device__ __forceinline__ R fold(R a, R, R, R, R) { return a; }
     template <bool W> static __device__ __forceinline__ R finish(R, const R* c, int) { return c[0]; }
 };
 template <typename R> struct Fn<kLinear, R> {        // c0 + sum pa_i x_i
+    static constexpr bool kLog2 = false;
     static __device__ __forceinline__ Prep prep(double w, double b, double pa, double) {
         return {pa * w, 0.0, pa * b};
     }
@@ -183,6 +185,7 @@ template <typename R> struct Fn<kLinear, R> {        // c0 + sum pa_i x_i
     template <bool W> static __device__ __forceinline__ R finish(R a, const R* c, int) { return c[0] + a; }
 };
 template <typename R> struct Fn<kSinSum, R> {        // sin(sum x_i), Eq. (1)
+    static constexpr bool kLog2 = false;
     static __device__ __forceinline__ Prep prep(double w, double b, double, double) {
         return {w, 0.0, b};
     }
@@ -191,6 +194,7 @@ template <typename R> struct Fn<kSinSum, R> {        // sin(sum x_i), Eq. (1)
     template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int) { return zsin<W>(a); }
 };
 template <typename R> struct Fn<kGaussNorm, R> {     // c1 exp(c0 |x|^2), Eq. (2)
+    static constexpr bool kLog2 = true;
     static __device__ __forceinline__ Prep prep(double w, double b, double, double) {
         return {w, b, 0.0};
     }
@@ -200,8 +204,12 @@ template <typename R> struct Fn<kGaussNorm, R> {     // c1 exp(c0 |x|^2), Eq. (2
         return fma(x, x, a);
     }
     template <bool W> static __device__ __forceinline__ R finish(R a, const R* c, int) { return c[1] * zexp(c[0] * a); }
+    // FP32 modes: log2 of the value over c1 (c2 = c0 log2 e); c1 in FP64
+    static __device__ __forceinline__ R finish_log2(R a, const R* c) { return c[2] * a; }
+    static __device__ __forceinline__ double value_scale(const Desc& D) { return D.c[1]; }
 };
 template <typename R> struct Fn<kGenzOsc, R> {       // cos(c0 + sum pa_i x_i)
+    static constexpr bool kLog2 = false;
     static __device__ __forceinline__ Prep prep(double w, double b, double pa, double) {
         return {pa * w, 0.0, pa * b};
     }
@@ -210,6 +218,7 @@ template <typename R> struct Fn<kGenzOsc, R> {       // cos(c0 + sum pa_i x_i)
     template <bool W> static __device__ __forceinline__ R finish(R a, const R* c, int) { return zcos<W>(c[0] + a); }
 };
 template <typename R> struct Fn<kGenzProdPeak, R> {  // 1 / prod (pb_i + (x_i - pa_i)^2)
+    static constexpr bool kLog2 = false;
     static __device__ __forceinline__ Prep prep(double w, double b, double pa, double) {
         return {w, b - pa, 0.0};
     }
@@ -221,6 +230,7 @@ template <typename R> struct Fn<kGenzProdPeak, R> {  // 1 / prod (pb_i + (x_i - 
     template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int) { return zrcp(a); }
 };
 template <typename R> struct Fn<kGenzGauss, R> {     // exp(-sum (pa_i (x_i - pb_i))^2)
+    static constexpr bool kLog2 = true;
     static __device__ __forceinline__ Prep prep(double w, double b, double pa, double pb) {
         return {pa * w, pa * (b - pb), 0.0};
     }
@@ -230,8 +240,11 @@ template <typename R> struct Fn<kGenzGauss, R> {     // exp(-sum (pa_i (x_i - pb
         return fma(t, t, a);
     }
     template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int) { return zexp(-a); }
+    static __device__ __forceinline__ R finish_log2(R a, const R*) { return -kLog2E * a; }
+    static __device__ __forceinline__ double value_scale(const Desc&) { return 1.0; }
 };
 template <typename R> struct Fn<kGenzCorner, R> {    // (1 + sum pa_i x_i)^-(d+1)
+    static constexpr bool kLog2 = false;
     static __device__ __forceinline__ Prep prep(double w, double b, double pa, double) {
         return {pa * w, 0.0, pa * b};
     }

@@ -116,6 +116,8 @@ def _load():
         "zmc_level_stats_noalloc": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p],
+        "zmc_check_expression": [ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t],
         "zmc_last_error": [H],
         "zmc_destroy": [H],
     }
@@ -289,6 +291,22 @@ def zmc_level_stats_noalloc(sums_ptr, cells, trials, n, volume, sigma_multiplier
         ctypes.c_void_p(int(sums_ptr)), int(cells), int(trials), int(n), float(volume),
         float(sigma_multiplier), ctypes.c_void_p(int(cell_stats_ptr)),
         ctypes.c_void_p(int(level_stats_ptr)), _stream_ptr(stream)))
+
+
+def zmc_check_expression(expr: str, dim: int, precision="fp64", cc=(10, 3)):
+    """Compile an expression integrand with NVRTC for compute capability cc
+    without a device.  Returns the compiler's log; raises ZmcError (with the
+    log) when it does not compile."""
+    mode = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    if expr.startswith("expr:"):
+        expr = expr[5:]
+    buf = ctypes.create_string_buffer(1 << 16)
+    rc = _lib.zmc_check_expression(expr.encode(), int(dim), mode, int(cc[0]), int(cc[1]), buf,
+                                   ctypes.sizeof(buf))
+    log = buf.value.decode(errors="replace")
+    if rc != ZMC_OK:
+        raise ZmcError(rc, log)
+    return log
 
 
 def zmc_last_error(h=None) -> str:

@@ -95,3 +95,33 @@ def test_integrate_without_integrand_reports_it(zmc):
         assert e.value.code == zmc.ZMC_ERR_NOINTEGRAND
     finally:
         zmc.zmc_destroy(h)
+
+
+# ------------------------------------------------------- expressions, no device
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_fp64acc", "fp32_kahan"])
+@pytest.mark.parametrize("expr,dim", [
+    ("sin(x[0] + x[1] + x[2])", 3),
+    ("(x[0] < p[0] ? p[1] : 0.0) * (1.0 + x[1])", 2),
+    ("exp(-(x[0]*x[0] + x[1]*x[1]) / 2e-4) * erf(x[2])", 3),
+    ("x[15] * x[0]", 16),
+])
+def test_expressions_compile_without_a_device(zmc, precision, expr, dim):
+    # the embedded device headers must compile under NVRTC in every mode
+    zmc.zmc_check_expression(expr, dim, precision, cc=(10, 3))
+
+
+def test_expression_compile_errors_without_a_device(zmc):
+    with pytest.raises(zmc.ZmcError) as e:
+        zmc.zmc_check_expression("x[0] + no_such_function(x[1])", 2, "fp32_fp64acc")
+    assert e.value.code == zmc.ZMC_ERR_COMPILE
+    assert "no_such_function" in str(e.value)
+    with pytest.raises(zmc.ZmcError) as e:
+        zmc.zmc_check_expression("x[0]; x[1]", 2)
+    assert e.value.code == zmc.ZMC_ERR_COMPILE
+    with pytest.raises(zmc.ZmcError) as e:
+        zmc.zmc_check_expression("x[0]", 17)
+    assert e.value.code == zmc.ZMC_ERR_ARG
+    with pytest.raises(zmc.ZmcError) as e:
+        zmc.zmc_check_expression("", 2)
+    assert e.value.code == zmc.ZMC_ERR_ARG

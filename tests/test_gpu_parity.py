@@ -170,3 +170,40 @@ def test_fp32_modes_within_stated_tolerance(zmc, w, _, prec):
     check_decisions_consistent(w, levels, res)
     exact = CF.integral(w.integrand, w.lo, w.hi, w.params)
     assert abs(res.value - exact) <= 4 * res.std + 1e-6 * abs(exact), (res.value, exact, res.std)
+
+
+@pytest.mark.parametrize("prec", ["fp32_fp64acc", "fp32_kahan"])
+def test_fp32_modes_keep_values_below_fp32_range(zmc, prec):
+    """Eq. (2) with a narrow peak (sigma 0.005 in 5-D): every level-1 value
+    lies far below FP32's range (the largest tile sum is ~1e-78), so only the
+    log2-domain evaluation of the FP32 modes sees the cell that holds the
+    peak and refines it.  Against the FP64 oracle on the same (FP32-stream)
+    points: the same cells and flags at every level, sums within the FP32
+    exponent's precision, and the same value and error."""
+    s = 0.005
+    w = Workload("gauss5_narrow", "gauss_norm", 5, [-1.0] * 5, [1.0] * 5, 3, 400, 4, 3, 2.0, 7,
+                 [s])
+    res, levels = run_gpu(zmc, w, prec)
+    ref = run_oracle(w, fp32_uniforms=True)
+    C = (math.sqrt(2 * math.pi) * s) ** -5
+    assert 0.0 < ref.levels[0].sums[..., 0].max() < 1e-38      # the range FP32 does not have
+    assert ref.flagged_per_level[0] == 1
+    assert res.levels_run == ref.levels_run
+    assert res.flagged_per_level == ref.flagged_per_level
+    for L, (g, r) in enumerate(zip(levels, ref.levels), start=1):
+        assert g["cells"] == r.coords.shape[0], L
+        # FP32 evaluation of exp(E), E = -|x|^2 / (2 s^2): the exponent's own
+        # rounding, |E| 2^-22, and the coordinates' (each off by up to
+        # 2^-22 max|x| through the FP32 cell coefficients) times the
+        # exponent's gradient |x| / s^2 = sqrt(2 |E|) / s, in d dimensions.
+        # A tile's largest value has |E| <= |ln(S1 / (n C))|.
+        s1 = r.sums[..., 0]
+        pos = s1 > 0
+        lnE = np.zeros_like(s1)
+        lnE[pos] = np.abs(np.log(s1[pos]) - math.log(w.n * C))
+        rtol = 2e-5 + 2.0 ** -22 * (lnE + w.dim * 1.0 * np.sqrt(2 * lnE) / s)
+        err = np.abs(g["sums"][..., 0] - s1)
+        assert np.all(err <= rtol * s1 + 1e-300), (L, float(np.max(err / (s1 + 1e-300))))
+        assert np.all((g["sums"][..., 0] > 0) == pos), L
+    assert math.isclose(res.value, ref.value, rel_tol=1e-3), (res.value, ref.value)
+    assert math.isclose(res.std, ref.std, rel_tol=1e-2), (res.std, ref.std)
