@@ -181,14 +181,16 @@ def fp32_flops_per_sample(integrand: str, d: int) -> int:
     """Counted FP32 flops per point of the FP32 modes (an FMA is 2, a multiply
     or add 1; the one hardware sine/cosine/exp2/reciprocal per point is an XU
     op, not a flop): the fold over the dimensions, the finishing function with
-    its range reduction (a multiply and two FMAs for sine and cosine), and the
-    reduction (S1 += f, S2 = fma(f, f, S2): 3)."""
+    its range reduction (sine and cosine in turns: a subtraction, the multiply
+    by 2 pi and the hardware sine's own scaling; the Gaussians in the log2
+    domain: the exponent's multiply and its offset from the lane's reference),
+    and the reduction (S1 += f, S2 = fma(f, f, S2): 3)."""
     if integrand == "genz_corner":
         e = d + 1
         return 2 * d + e.bit_length() + bin(e).count("1") + 3
-    per = {"constant": 3, "linear": 2 * d + 4, "sin_sum": 2 * d + 8,
-           "gauss_norm": 4 * d + 6, "genz_osc": 2 * d + 9, "genz_prodpeak": 5 * d + 3,
-           "genz_gauss": 4 * d + 4}
+    per = {"constant": 3, "linear": 2 * d + 4, "sin_sum": 2 * d + 6,
+           "gauss_norm": 4 * d + 5, "genz_osc": 2 * d + 7, "genz_prodpeak": 5 * d + 3,
+           "genz_gauss": 4 * d + 5}
     return per[integrand]
 
 
@@ -220,8 +222,8 @@ def algorithmic_bytes_per_launch(cells_per_level, n, trials, fp64):
 # kernel's sources it was taken on (profiles/zmc_eval_reduce_sin6d_traffic.md).
 TRAFFIC_CAPTURE = {
     "workload": "sin6d", "fp64": False,
-    "bytes_per_launch": (235520 + 0 + 10405888 + 171250432) / 2,
-    "sources_sha256": "7e93858380265d8339f9d1b698307c80cc792672b32dee04d39d76412e22c431",
+    "bytes_per_launch": (333056 + 0 + 10340352 + 168202752) / 2,
+    "sources_sha256": "fe21431db174f74dd7bb7b4f871992908e1d2b33f872c851ff68771a6e7fce0d",
 }
 KERNEL_SOURCES = ["eval_kernel.cuh", "zmc_device.cuh", "zmc_layout.h", "eval_fp32.cu"]
 

@@ -17,9 +17,9 @@
 #include "zmc_internal.h"
 
 namespace zmc {
-const void* eval_kernel_fp64(int fn, bool wide);
-const void* eval_kernel_fp32_fp64acc(int fn, bool wide);
-const void* eval_kernel_fp32_kahan(int fn, bool wide);
+const void* eval_kernel_fp64(int fn);
+const void* eval_kernel_fp32_fp64acc(int fn);
+const void* eval_kernel_fp32_kahan(int fn);
 }  // namespace zmc
 
 using namespace zmc;
@@ -142,6 +142,7 @@ void fill_integrand(Desc& D, int id, const std::vector<double>& p) {
     }
     case kGenzOsc:
         D.c[0] = 2.0 * M_PI * p[0];
+        D.c[1] = p[0];                    // the phase in turns (FP32 modes)
         for (int i = 0; i < d; ++i) D.pa[i] = p[1 + i];
         break;
     case kGenzProdPeak:
@@ -298,36 +299,20 @@ void build_desc(const zmc_ctx* h, Desc& D) {
     }
 }
 
-// Bound on |argument| of the sine / cosine over the box, for the FP32
-// kernels' choice between the bounded and the any-argument reduction.
-double trig_argument_bound(const zmc_ctx* h) {
-    double b = 0.0;
-    for (int i = 0; i < h->dim; ++i) {
-        const double r = std::max(fabs(h->lo[i]), fabs(h->hi[i]));
-        if (h->integrand == kSinSum) b += r;
-        else if (h->integrand == kGenzOsc) b += fabs(h->params[1 + i]) * r;
-    }
-    if (h->integrand == kGenzOsc) b += fabs(2.0 * M_PI * h->params[0]);
-    return b;
-}
-
-const void* batch_kernel(int mode, int fn, bool wide) {
+const void* batch_kernel(int mode, int fn) {
     switch (mode) {
-    case ZMC_FP64: return batch_kernel_fp64(fn, wide);
-    case ZMC_FP32_FP64ACC: return batch_kernel_fp32_fp64acc(fn, wide);
-    default: return batch_kernel_fp32_kahan(fn, wide);
+    case ZMC_FP64: return batch_kernel_fp64(fn);
+    case ZMC_FP32_FP64ACC: return batch_kernel_fp32_fp64acc(fn);
+    default: return batch_kernel_fp32_kahan(fn);
     }
 }
 
 const void* eval_kernel(const zmc_ctx* h) {
     if (h->integrand == kExpression) return h->jit.kernel;
-    // 8192 is the FP32 reduction's limit; the margin covers FP32 rounding of
-    // the accumulated argument.
-    const bool wide = trig_argument_bound(h) > 0.99 * 8192.0;
     switch (h->mode) {
-    case ZMC_FP64: return eval_kernel_fp64(h->integrand, wide);
-    case ZMC_FP32_FP64ACC: return eval_kernel_fp32_fp64acc(h->integrand, wide);
-    default: return eval_kernel_fp32_kahan(h->integrand, wide);
+    case ZMC_FP64: return eval_kernel_fp64(h->integrand);
+    case ZMC_FP32_FP64ACC: return eval_kernel_fp32_fp64acc(h->integrand);
+    default: return eval_kernel_fp32_kahan(h->integrand);
     }
 }
 
@@ -548,13 +533,13 @@ int finish_result(zmc_ctx* h, zmc_result* out) {
 
 // Device tables and per-level graphs of the last batch, reused while the
 // same handles (same buffers, precision and depth) come back.
-// Integrals of a batch that share a sampling kernel (integrand and trig
-// variant): a contiguous range of the device table.
+// Integrals of a batch that share a sampling kernel (same integrand): a
+// contiguous range of the device table.
 struct BatchGroup {
     const void* kernel;
     int start, count, grid;
 };
-constexpr int kMaxBatchGroups = 2 * kNumIntegrands;
+constexpr int kMaxBatchGroups = kNumIntegrands;
 
 struct BatchCache {
     int device = -1, capacity = 0;
@@ -929,15 +914,14 @@ ZMC_API int zmc_integrate_batch(int count, const zmc_handle* hs, void* stream,
         ev[i].parents[1] = h->buf.parents[1];
         ev[i].keys = philox_keys(h->seed);
         ev[i].fn = h->integrand;
-        ev[i].wide = trig_argument_bound(h) > 0.99 * 8192.0 ? 1 : 0;
-        kern[i] = batch_kernel(mode, ev[i].fn, ev[i].wide != 0);
+        kern[i] = batch_kernel(mode, ev[i].fn);
         l1[i] = ipow_sat(h->k, h->dim, INT64_MAX);
         build_desc(h, B.h_desc[i]);
     }
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return std::make_pair(ev[a].fn, ev[a].wide) < std::make_pair(ev[b].fn, ev[b].wide);
+        return ev[a].fn < ev[b].fn;
     });
     std::vector<BatchEval> ev_sorted(count);
     std::vector<BatchGroup> groups;

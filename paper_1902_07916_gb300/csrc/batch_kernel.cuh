@@ -1,5 +1,5 @@
 // Batched sampling kernel (kernel (a) over many integrals).  One persistent
-// kernel per (integrand, trig-variant) group of a batch: its warps pop work
+// kernel per integrand group of a batch: its warps pop work
 // units of the group's integrals from an atomic queue, find the unit's
 // integral by binary search in the group's prefix sums and run the unit
 // exactly as the single-integral kernel would (same unit decomposition, same
@@ -21,7 +21,7 @@ template <int MODE>
 constexpr int batch_min_blocks() { return MODE == ZMC_FP64 ? eval_min_blocks<MODE>() : 3; }
 static_assert(kBatchThreads == kEvalMaxThreads, "shared slices are sized for kEvalMaxThreads");
 
-template <int MODE, int FN, bool WIDE>
+template <int MODE, int FN>
 __global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<MODE>())
 zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
                const int64_t* __restrict__ offsets, unsigned long long* head) {
@@ -64,7 +64,7 @@ zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
         SumsFor<MODE, FN> acc(slot, value_scale<MODE, FN>(D));
 #define ZMC_BATCH_CASE(DD)                                                                    \
     case DD:                                                                                  \
-        sample_unit_fold<MODE, FN, WIDE, DD>(acc, keys, sc, wc, wp, wcst, start, un.g0, un.g1, \
+        sample_unit_fold<MODE, FN, DD>(acc, keys, sc, wc, wp, wcst, start, un.g0, un.g1, \
                                              plan.ngroups - 1, plan.tail);                     \
         break;
         switch (D.d) {
@@ -82,21 +82,16 @@ zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
 
 // One mode's batched instantiations, indexed like eval_kernel_for().
 template <int MODE>
-inline const void* batch_kernel_for(int fn, bool wide) {
-    const bool w = wide && MODE != ZMC_FP64;
+inline const void* batch_kernel_for(int fn) {
     switch (fn) {
-    case kConstant: return (const void*)zmc_batch_eval<MODE, kConstant, false>;
-    case kLinear: return (const void*)zmc_batch_eval<MODE, kLinear, false>;
-    case kSinSum:
-        return w ? (const void*)zmc_batch_eval<MODE, kSinSum, true>
-                 : (const void*)zmc_batch_eval<MODE, kSinSum, false>;
-    case kGaussNorm: return (const void*)zmc_batch_eval<MODE, kGaussNorm, false>;
-    case kGenzOsc:
-        return w ? (const void*)zmc_batch_eval<MODE, kGenzOsc, true>
-                 : (const void*)zmc_batch_eval<MODE, kGenzOsc, false>;
-    case kGenzProdPeak: return (const void*)zmc_batch_eval<MODE, kGenzProdPeak, false>;
-    case kGenzGauss: return (const void*)zmc_batch_eval<MODE, kGenzGauss, false>;
-    case kGenzCorner: return (const void*)zmc_batch_eval<MODE, kGenzCorner, false>;
+    case kConstant: return (const void*)zmc_batch_eval<MODE, kConstant>;
+    case kLinear: return (const void*)zmc_batch_eval<MODE, kLinear>;
+    case kSinSum: return (const void*)zmc_batch_eval<MODE, kSinSum>;
+    case kGaussNorm: return (const void*)zmc_batch_eval<MODE, kGaussNorm>;
+    case kGenzOsc: return (const void*)zmc_batch_eval<MODE, kGenzOsc>;
+    case kGenzProdPeak: return (const void*)zmc_batch_eval<MODE, kGenzProdPeak>;
+    case kGenzGauss: return (const void*)zmc_batch_eval<MODE, kGenzGauss>;
+    case kGenzCorner: return (const void*)zmc_batch_eval<MODE, kGenzCorner>;
     default: return nullptr;
     }
 }

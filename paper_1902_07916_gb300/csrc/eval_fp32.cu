@@ -2,7 +2,5 @@
 #include "eval_kernel.cuh"
 
 namespace zmc {
-const void* eval_kernel_fp32_fp64acc(int fn, bool wide) {
-    return eval_kernel_for<ZMC_FP32_FP64ACC>(fn, wide);
-}
+const void* eval_kernel_fp32_fp64acc(int fn) { return eval_kernel_for<ZMC_FP32_FP64ACC>(fn); }
 }  // namespace zmc

@@ -2,5 +2,5 @@
 #include "eval_kernel.cuh"
 
 namespace zmc {
-const void* eval_kernel_fp64(int fn, bool wide) { return eval_kernel_for<ZMC_FP64>(fn, wide); }
+const void* eval_kernel_fp64(int fn) { return eval_kernel_for<ZMC_FP64>(fn); }
 }  // namespace zmc

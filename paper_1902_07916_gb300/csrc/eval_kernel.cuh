@@ -378,7 +378,7 @@ __device__ __forceinline__ typename ModeTraits<MODE>::R fold_setup(
 // Philox block of every dimension (round 1's product A * c0 given as P, the
 // 64-bit product for dimension 0), each folded into the G running sums, then
 // the finishing function.
-template <int MODE, int FN, bool WIDE, int DIM>
+template <int MODE, int FN, int DIM>
 __device__ __forceinline__ void group_values(
     const PhiloxKeys& keys, const StreamConst& sc,
     const typename ModeTraits<MODE>::R2* w_coef, const typename ModeTraits<MODE>::R* s_pb,
@@ -407,7 +407,7 @@ __device__ __forceinline__ void group_values(
         for (int p = 0; p < G; ++p) f[p] = F::finish_log2(a[p], s_c);
     } else {
 #pragma unroll
-        for (int p = 0; p < G; ++p) f[p] = F::template finish<WIDE>(a[p], s_c, nd);
+        for (int p = 0; p < G; ++p) f[p] = F::finish(a[p], s_c, nd);
     }
 }
 
@@ -417,7 +417,7 @@ __device__ __forceinline__ void group_values(
 // grows by one per dimension and by 32*d per group of this lane.  Only the
 // tile's last group can hold points past n; it is left out of the main loop
 // and run, masked, by the one lane it falls to in the unit that holds it.
-template <int MODE, int FN, bool WIDE, int DIM>
+template <int MODE, int FN, int DIM>
 __device__ __forceinline__ void sample_unit_fold(
     SumsFor<MODE, FN>& acc, const PhiloxKeys& keys, const StreamConst& sc,
     const typename ModeTraits<MODE>::R2* w_coef, const typename ModeTraits<MODE>::R* s_pb,
@@ -433,21 +433,21 @@ __device__ __forceinline__ void sample_unit_fold(
     while (g < full_end) {
         for (int j = 0; j < kFlushGroups && g < full_end; ++j, g += 32, Pg += step) {
             R f[G];
-            group_values<MODE, FN, WIDE, DIM>(keys, sc, w_coef, s_pb, s_c, start, Pg, nd, f);
+            group_values<MODE, FN, DIM>(keys, sc, w_coef, s_pb, s_c, start, Pg, nd, f);
             acc.add(f);
         }
         acc.flush();
     }
     if (g == last_group && g < g1) {
         R f[G];
-        group_values<MODE, FN, WIDE, DIM>(keys, sc, w_coef, s_pb, s_c, start, Pg, nd, f);
+        group_values<MODE, FN, DIM>(keys, sc, w_coef, s_pb, s_c, start, Pg, nd, f);
         mask_tail(true, tail, f, log_domain<MODE, FN>() ? R(neg_inf()) : R(0));
         acc.add(f);
         acc.flush();
     }
 }
 
-template <int MODE, int FN, bool WIDE>
+template <int MODE, int FN>
 __global__ void __launch_bounds__(kEvalMaxThreads, eval_min_blocks<MODE>())
 zmc_eval_reduce(const Desc* __restrict__ desc, State* st,
                 const uint32_t* __restrict__ parents, double2* __restrict__ partial,
@@ -478,7 +478,7 @@ zmc_eval_reduce(const Desc* __restrict__ desc, State* st,
         SumsFor<MODE, FN> acc(slot, value_scale<MODE, FN>(D));
 #define ZMC_FOLD_CASE(DD)                                                                      \
     case DD:                                                                                   \
-        sample_unit_fold<MODE, FN, WIDE, DD>(acc, keys, sc, s_coef[warp], s_pb, s_c, start,    \
+        sample_unit_fold<MODE, FN, DD>(acc, keys, sc, s_coef[warp], s_pb, s_c, start,    \
                                              un.g0, un.g1, plan.ngroups - 1, plan.tail);       \
         break;
         switch (d) {
@@ -562,25 +562,18 @@ __device__ __forceinline__ void eval_expr_body(const Desc* __restrict__ desc,
 }
 
 #ifndef __CUDACC_RTC__
-// One mode's registry instantiations, indexed by integrand id.  `wide`
-// selects the sine/cosine variants that accept any argument; the host
-// chooses the bounded ones when it can prove |argument| <= kFastTrigLimit.
+// One mode's registry instantiations, indexed by integrand id.
 template <int MODE>
-inline const void* eval_kernel_for(int fn, bool wide) {
-    const bool w = wide && MODE != ZMC_FP64;
+inline const void* eval_kernel_for(int fn) {
     switch (fn) {
-    case kConstant: return (const void*)zmc_eval_reduce<MODE, kConstant, false>;
-    case kLinear: return (const void*)zmc_eval_reduce<MODE, kLinear, false>;
-    case kSinSum:
-        return w ? (const void*)zmc_eval_reduce<MODE, kSinSum, true>
-                 : (const void*)zmc_eval_reduce<MODE, kSinSum, false>;
-    case kGaussNorm: return (const void*)zmc_eval_reduce<MODE, kGaussNorm, false>;
-    case kGenzOsc:
-        return w ? (const void*)zmc_eval_reduce<MODE, kGenzOsc, true>
-                 : (const void*)zmc_eval_reduce<MODE, kGenzOsc, false>;
-    case kGenzProdPeak: return (const void*)zmc_eval_reduce<MODE, kGenzProdPeak, false>;
-    case kGenzGauss: return (const void*)zmc_eval_reduce<MODE, kGenzGauss, false>;
-    case kGenzCorner: return (const void*)zmc_eval_reduce<MODE, kGenzCorner, false>;
+    case kConstant: return (const void*)zmc_eval_reduce<MODE, kConstant>;
+    case kLinear: return (const void*)zmc_eval_reduce<MODE, kLinear>;
+    case kSinSum: return (const void*)zmc_eval_reduce<MODE, kSinSum>;
+    case kGaussNorm: return (const void*)zmc_eval_reduce<MODE, kGaussNorm>;
+    case kGenzOsc: return (const void*)zmc_eval_reduce<MODE, kGenzOsc>;
+    case kGenzProdPeak: return (const void*)zmc_eval_reduce<MODE, kGenzProdPeak>;
+    case kGenzGauss: return (const void*)zmc_eval_reduce<MODE, kGenzGauss>;
+    case kGenzCorner: return (const void*)zmc_eval_reduce<MODE, kGenzCorner>;
     default: return nullptr;
     }
 }

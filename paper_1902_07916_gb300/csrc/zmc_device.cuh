@@ -105,48 +105,19 @@ __device__ __forceinline__ void fields_1m(uint4 w, float& v0, float& v1, float& 
 }
 
 // ------------------------------------------------ elementary functions
-// FP64 mode uses the CUDA math library.  FP32 mode reduces the argument of
-// sin/cos by 2 pi with a two-constant Cody-Waite step (Cody and Waite, 1980;
-// 2 pi split into a 13-bit head, so k * head is exact for |k| < 2^11, and a
-// tail) and evaluates the hardware sine/cosine on [-pi, pi] (absolute error
-// about 2^-21); exp goes through the hardware 2^x.  Arguments beyond the
-// reduction's range are reduced in FP64 instead (a rare, slower path).
-constexpr float kTwoPiHead = 0x1.922p+2f;        // 2 pi to 13 significant bits
-constexpr float kTwoPiTail = -0x1.2aeef4p-16f;   // 2 pi - head, to FP32
-constexpr float kInvTwoPi = 0x1.45f306p-3f;      // 1 / (2 pi), to FP32
-constexpr float kFastTrigLimit = 8192.0f;        // |k| <= 1304 < 2^11
+// FP64 mode uses the CUDA math library.  FP32 mode carries the argument of
+// sin/cos in turns (the per-cell fold coefficients are scaled by 1/(2 pi) in
+// FP64): t - rint(t) is then an exact reduction for every float t, and the
+// hardware sine/cosine takes the reduced turn times 2 pi, within [-pi, pi]
+// (absolute error about 2^-21).  exp goes through the hardware 2^x.
+constexpr float kTwoPi = 0x1.921fb6p+2f;         // 2 pi, to FP32
+constexpr double kInvTwoPiD = 0.15915494309189535;  // 1 / (2 pi)
 constexpr float kLog2E = 0x1.715476p+0f;         // log2(e), to FP32
 
-__device__ __forceinline__ float reduce_two_pi(float x) {
-    const float k = rintf(x * kInvTwoPi);
-    return fmaf(-k, kTwoPiTail, fmaf(-k, kTwoPiHead, x));
-}
-static __device__ __noinline__ float reduce_two_pi_wide(float x) {
-    const double xd = (double)x;
-    const double k = rint(xd * 0.15915494309189535);            // 1 / (2 pi)
-    return (float)fma(-k, 2.4492935982947064e-16, fma(-k, 6.283185307179586, xd));
-}
-// WIDE = false: the caller has proven |x| <= kFastTrigLimit.
-template <bool WIDE>
-__device__ __forceinline__ float zsin(float x) {
-    if constexpr (WIDE)
-        return __sinf(fabsf(x) <= kFastTrigLimit ? reduce_two_pi(x) : reduce_two_pi_wide(x));
-    else
-        return __sinf(reduce_two_pi(x));
-}
-template <bool WIDE>
-__device__ __forceinline__ float zcos(float x) {
-    if constexpr (WIDE)
-        return __cosf(fabsf(x) <= kFastTrigLimit ? reduce_two_pi(x) : reduce_two_pi_wide(x));
-    else
-        return __cosf(reduce_two_pi(x));
-}
+__device__ __forceinline__ float zsin_turns(float t) { return __sinf((t - rintf(t)) * kTwoPi); }
+__device__ __forceinline__ float zcos_turns(float t) { return __cosf((t - rintf(t)) * kTwoPi); }
 __device__ __forceinline__ float zexp(float x) { return exp2f(x * kLog2E); }
 __device__ __forceinline__ float zrcp(float x) { return __frcp_rn(x); }
-template <bool WIDE>
-__device__ __forceinline__ double zsin(double x) { return sin(x); }
-template <bool WIDE>
-__device__ __forceinline__ double zcos(double x) { return cos(x); }
 __device__ __forceinline__ double zexp(double x) { return exp(x); }
 __device__ __forceinline__ double zrcp(double x) { return 1.0 / x; }
 
@@ -173,7 +144,7 @@ template <typename R> struct Fn<kConstant, R> {      // c0
     static __device__ __forceinline__ Prep prep(double, double, double, double) { return {0, 0, 0}; }
     static __device__ __forceinline__ R init() { return R(0); }
     static __device__ __forceinline__ R fold(R a, R, R, R, R) { return a; }
-    template <bool W> static __device__ __forceinline__ R finish(R, const R* c, int) { return c[0]; }
+    static __device__ __forceinline__ R finish(R, const R* c, int) { return c[0]; }
 };
 template <typename R> struct Fn<kLinear, R> {        // c0 + sum pa_i x_i
     static constexpr bool kLog2 = false;
@@ -182,16 +153,20 @@ template <typename R> struct Fn<kLinear, R> {        // c0 + sum pa_i x_i
     }
     static __device__ __forceinline__ R init() { return R(0); }
     static __device__ __forceinline__ R fold(R a, R v, R al, R, R) { return fma(al, v, a); }
-    template <bool W> static __device__ __forceinline__ R finish(R a, const R* c, int) { return c[0] + a; }
+    static __device__ __forceinline__ R finish(R a, const R* c, int) { return c[0] + a; }
 };
 template <typename R> struct Fn<kSinSum, R> {        // sin(sum x_i), Eq. (1)
     static constexpr bool kLog2 = false;
+    static constexpr double kScale = sizeof(R) == 4 ? kInvTwoPiD : 1.0;  // FP32: turns
     static __device__ __forceinline__ Prep prep(double w, double b, double, double) {
-        return {w, 0.0, b};
+        return {w * kScale, 0.0, b * kScale};
     }
     static __device__ __forceinline__ R init() { return R(0); }
     static __device__ __forceinline__ R fold(R a, R v, R al, R, R) { return fma(al, v, a); }
-    template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int) { return zsin<W>(a); }
+    static __device__ __forceinline__ R finish(R a, const R*, int) {
+        if constexpr (sizeof(R) == 4) return zsin_turns(a);
+        else return sin(a);
+    }
 };
 template <typename R> struct Fn<kGaussNorm, R> {     // c1 exp(c0 |x|^2), Eq. (2)
     static constexpr bool kLog2 = true;
@@ -203,19 +178,24 @@ template <typename R> struct Fn<kGaussNorm, R> {     // c1 exp(c0 |x|^2), Eq. (2
         const R x = fma(v, al, be);
         return fma(x, x, a);
     }
-    template <bool W> static __device__ __forceinline__ R finish(R a, const R* c, int) { return c[1] * zexp(c[0] * a); }
+    static __device__ __forceinline__ R finish(R a, const R* c, int) { return c[1] * zexp(c[0] * a); }
     // FP32 modes: log2 of the value over c1 (c2 = c0 log2 e); c1 in FP64
     static __device__ __forceinline__ R finish_log2(R a, const R* c) { return c[2] * a; }
     static __device__ __forceinline__ double value_scale(const Desc& D) { return D.c[1]; }
 };
 template <typename R> struct Fn<kGenzOsc, R> {       // cos(c0 + sum pa_i x_i)
     static constexpr bool kLog2 = false;
+    static constexpr double kScale = sizeof(R) == 4 ? kInvTwoPiD : 1.0;  // FP32: turns
     static __device__ __forceinline__ Prep prep(double w, double b, double pa, double) {
-        return {pa * w, 0.0, pa * b};
+        return {pa * w * kScale, 0.0, pa * b * kScale};
     }
     static __device__ __forceinline__ R init() { return R(0); }
     static __device__ __forceinline__ R fold(R a, R v, R al, R, R) { return fma(al, v, a); }
-    template <bool W> static __device__ __forceinline__ R finish(R a, const R* c, int) { return zcos<W>(c[0] + a); }
+    // c0 = 2 pi u1 in radians; c1 = u1, the same phase in turns
+    static __device__ __forceinline__ R finish(R a, const R* c, int) {
+        if constexpr (sizeof(R) == 4) return zcos_turns(c[1] + a);
+        else return cos(c[0] + a);
+    }
 };
 template <typename R> struct Fn<kGenzProdPeak, R> {  // 1 / prod (pb_i + (x_i - pa_i)^2)
     static constexpr bool kLog2 = false;
@@ -227,7 +207,7 @@ template <typename R> struct Fn<kGenzProdPeak, R> {  // 1 / prod (pb_i + (x_i - 
         const R t = fma(v, al, be);
         return a * fma(t, t, pb);
     }
-    template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int) { return zrcp(a); }
+    static __device__ __forceinline__ R finish(R a, const R*, int) { return zrcp(a); }
 };
 template <typename R> struct Fn<kGenzGauss, R> {     // exp(-sum (pa_i (x_i - pb_i))^2)
     static constexpr bool kLog2 = true;
@@ -239,7 +219,7 @@ template <typename R> struct Fn<kGenzGauss, R> {     // exp(-sum (pa_i (x_i - pb
         const R t = fma(v, al, be);
         return fma(t, t, a);
     }
-    template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int) { return zexp(-a); }
+    static __device__ __forceinline__ R finish(R a, const R*, int) { return zexp(-a); }
     static __device__ __forceinline__ R finish_log2(R a, const R*) { return -kLog2E * a; }
     static __device__ __forceinline__ double value_scale(const Desc&) { return 1.0; }
 };
@@ -250,7 +230,7 @@ template <typename R> struct Fn<kGenzCorner, R> {    // (1 + sum pa_i x_i)^-(d+1
     }
     static __device__ __forceinline__ R init() { return R(1); }
     static __device__ __forceinline__ R fold(R a, R v, R al, R, R) { return fma(al, v, a); }
-    template <bool W> static __device__ __forceinline__ R finish(R a, const R*, int d) {
+    static __device__ __forceinline__ R finish(R a, const R*, int d) {
         // r^(d+1) with r = 1/a, by binary powering
         R r = zrcp(a), p = R(1);
         for (int e = d + 1; e; e >>= 1) {

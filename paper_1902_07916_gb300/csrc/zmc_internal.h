@@ -67,16 +67,16 @@ struct BatchEval {
     double2* sums;
     const uint32_t* parents[2];
     PhiloxKeys keys;
-    int32_t fn, wide;
+    int32_t fn;
 };
 
 // Batched form (batch.cu, select.cu): `items` / `level1_cells` / `out` are
 // device arrays of `count` entries; row y of each selection grid works on
 // integral y.
 // Batched sampling kernels of one mode by integrand (eval_fp*.cu).
-const void* batch_kernel_fp64(int fn, bool wide);
-const void* batch_kernel_fp32_fp64acc(int fn, bool wide);
-const void* batch_kernel_fp32_kahan(int fn, bool wide);
+const void* batch_kernel_fp64(int fn);
+const void* batch_kernel_fp32_fp64acc(int fn);
+const void* batch_kernel_fp32_kahan(int fn);
 // Plan + sampling kernel of one group of `count` integrals (same integrand):
 // `offsets` has count + 1 entries, `head` is the group's queue counter.
 cudaError_t launch_batch_level(const BatchEval* items, int count, int level, int64_t* offsets,

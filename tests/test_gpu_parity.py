@@ -207,3 +207,23 @@ def test_fp32_modes_keep_values_below_fp32_range(zmc, prec):
         assert np.all((g["sums"][..., 0] > 0) == pos), L
     assert math.isclose(res.value, ref.value, rel_tol=1e-3), (res.value, ref.value)
     assert math.isclose(res.std, ref.std, rel_tol=1e-2), (res.std, ref.std)
+
+
+@pytest.mark.parametrize("prec", ["fp32_fp64acc", "fp32_kahan"])
+def test_fp32_sine_of_large_arguments(zmc, prec):
+    """sin(x1 + x2 + x3) on [3000, 3010]^3: arguments near 9000 rad (1430
+    turns).  The FP32 modes fold the argument in turns and reduce it by
+    t - rint(t), exact for any float; what remains is FP32's rounding of the
+    argument itself, (d + 2) ulp of |t| at most, times 2 pi.  Level-1 sums
+    against the oracle on the same points within n times that, identical
+    flags, value within the same bound."""
+    w = Workload("sin3_far", "sin_sum", 3, [3000.0] * 3, [3010.0] * 3, 4, 500, 4, 2, 2.0, 3)
+    res, levels = run_gpu(zmc, w, prec)
+    ref = run_oracle(w, fp32_uniforms=True)
+    t_max = sum(w.hi) / (2 * math.pi)
+    e_point = (w.dim + 2) * 2.0 ** -24 * t_max * 2 * math.pi
+    err = np.abs(levels[0]["sums"][..., 0] - ref.levels[0].sums[..., 0])
+    assert np.all(err <= w.n * e_point), (float(err.max()), w.n * e_point)
+    assert res.flagged_per_level == ref.flagged_per_level
+    exact = CF.integral(w.integrand, w.lo, w.hi, w.params)
+    assert abs(res.value - exact) <= 4 * res.std + 1e-3 * abs(exact), (res.value, exact, res.std)
