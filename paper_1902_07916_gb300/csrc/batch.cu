@@ -1,6 +1,6 @@
 // Batched integration: many independent integrals (uneven dimension, cell
 // count and depth) advance one tree level at a time.  The integrals are
-// grouped by integrand (and trig variant); per level and group:
+// grouped by integrand; per level and group:
 //   1. zmc_batch_plan: each integral's number of sampling units at this level
 //      (from its own tree state) and their exclusive prefix sum;
 //   2. zmc_batch_eval (batch_kernel.cuh): one persistent kernel over the
