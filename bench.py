@@ -31,6 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Gsamples/s per GB300 (stratified MC + tree search, sin(sum x) 6-D)"
+INTEGRAND_TEXT = {"sin_sum": "sin(sum x)", "gauss_norm": "normalised Gaussian",
+                  "genz_corner": "Genz corner peak", "genz_gauss": "Genz Gaussian",
+                  "genz_osc": "Genz oscillatory", "genz_prodpeak": "Genz product peak"}
 UNIT = "Gsamples/s"
 
 
@@ -375,9 +378,10 @@ def run_ours(args, world, rank, local):
         "dtype": "f32 eval / f64 accum" if prec == zmc.ZMC_FP32_FP64ACC else args.precision,
         "data": "synthetic (analytic integrand, Philox counter-based points)",
         "config": {
-            "workload": "%s: sin(sum x) on [0,10]^%d, k=%d, n=%d, trials=%d, depth=%d, m=%g, "
+            "workload": "%s: %s on [%g,%g]^%d, k=%d, n=%d, trials=%d, depth=%d, m=%g, "
                         "budget 2^24 cells/level, 2^40 points/run" % (
-                            w.name, w.dim, w.k, w.n, w.trials, w.depth, w.sigma_multiplier),
+                            w.name, INTEGRAND_TEXT.get(w.integrand, w.integrand), w.lo[0],
+                            w.hi[0], w.dim, w.k, w.n, w.trials, w.depth, w.sigma_multiplier),
             "precision": args.precision, "seed": w.seed, "parallelism": "replicas x%d" % world,
             "l2": "flushed between steps (256 MiB write, outside the timed events)",
             "samples_per_step": r.samples, "levels_run": r.levels_run,
