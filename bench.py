@@ -225,8 +225,8 @@ def algorithmic_bytes_per_launch(cells_per_level, n, trials, fp64):
 # kernel's sources it was taken on (profiles/zmc_eval_reduce_sin6d_traffic.md).
 TRAFFIC_CAPTURE = {
     "workload": "sin6d", "fp64": False,
-    "bytes_per_launch": (333056 + 0 + 10340352 + 168202752) / 2,
-    "sources_sha256": "fe21431db174f74dd7bb7b4f871992908e1d2b33f872c851ff68771a6e7fce0d",
+    "bytes_per_launch": (70912 + 0 + 10710016 + 170334976) / 2,
+    "sources_sha256": "d93fbc690bb856550d4dcf8f44e5e9563b3bda61e3ab373b86c91b795c7c445c",
 }
 KERNEL_SOURCES = ["eval_kernel.cuh", "zmc_device.cuh", "zmc_layout.h", "eval_fp32.cu"]
 

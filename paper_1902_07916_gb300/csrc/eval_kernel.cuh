@@ -534,26 +534,40 @@ __device__ __forceinline__ void eval_expr_body(const Desc* __restrict__ desc,
         __syncwarp();
         const StreamConst sc = stream_const(keys, un.t, (uint32_t)un.q, (uint32_t)level);
         LaneSums<MODE> acc(slot);
+        // the G points of group gg: coordinates from the blocks, then E
+        auto values = [&](uint32_t gg, R (&f)[G]) {
+            R x[G][DIM];
+            const uint32_t cbase = gg * DIM;
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) {
+                const uint4 w = philox_stream(keys, sc, cbase + i);
+                const R2 c = wb[i];
+                R v[G];
+                block_points<MODE>(w, v);
+#pragma unroll
+                for (int p = 0; p < G; ++p) x[p][i] = fma(v[p], c.x, c.y);
+            }
+#pragma unroll
+            for (int p = 0; p < G; ++p) f[p] = E::eval(x[p], s_p);
+        };
+        // as in sample_unit_fold: the tile's last group, the only one that
+        // can run past n, is left to the one lane it falls to
+        const uint32_t last = plan.ngroups - 1;
+        const uint32_t full_end = un.g1 <= last ? un.g1 : last;
         uint32_t g = un.g0 + lane;
-        while (g < un.g1) {
-            for (int j = 0; j < kFlushGroups && g < un.g1; ++j, g += 32) {
-                R x[G][DIM];
-                const uint32_t cbase = g * DIM;
-#pragma unroll
-                for (int i = 0; i < DIM; ++i) {
-                    const uint4 w = philox_stream(keys, sc, cbase + i);
-                    const R2 c = wb[i];
-                    R v[G];
-                    block_points<MODE>(w, v);
-#pragma unroll
-                    for (int p = 0; p < G; ++p) x[p][i] = fma(v[p], c.x, c.y);
-                }
+        while (g < full_end) {
+            for (int j = 0; j < kFlushGroups && g < full_end; ++j, g += 32) {
                 R f[G];
-#pragma unroll
-                for (int p = 0; p < G; ++p) f[p] = E::eval(x[p], s_p);
-                mask_tail(g == plan.ngroups - 1, plan.tail, f);
+                values(g, f);
                 acc.add(f);
             }
+            acc.flush();
+        }
+        if (g == last && g < un.g1) {
+            R f[G];
+            values(g, f);
+            mask_tail(true, plan.tail, f);
+            acc.add(f);
             acc.flush();
         }
         acc.reduce_store(partial + u);
