@@ -17,9 +17,9 @@
 #include "zmc_internal.h"
 
 namespace zmc {
-const void* eval_kernel_fp64(int fn);
-const void* eval_kernel_fp32_fp64acc(int fn);
-const void* eval_kernel_fp32_kahan(int fn);
+const void* eval_kernel_fp64(int fn, int d);
+const void* eval_kernel_fp32_fp64acc(int fn, int d);
+const void* eval_kernel_fp32_kahan(int fn, int d);
 }  // namespace zmc
 
 using namespace zmc;
@@ -299,20 +299,20 @@ void build_desc(const zmc_ctx* h, Desc& D) {
     }
 }
 
-const void* batch_kernel(int mode, int fn) {
+const void* batch_kernel(int mode, int fn, int d) {
     switch (mode) {
-    case ZMC_FP64: return batch_kernel_fp64(fn);
-    case ZMC_FP32_FP64ACC: return batch_kernel_fp32_fp64acc(fn);
-    default: return batch_kernel_fp32_kahan(fn);
+    case ZMC_FP64: return batch_kernel_fp64(fn, d);
+    case ZMC_FP32_FP64ACC: return batch_kernel_fp32_fp64acc(fn, d);
+    default: return batch_kernel_fp32_kahan(fn, d);
     }
 }
 
 const void* eval_kernel(const zmc_ctx* h) {
     if (h->integrand == kExpression) return h->jit.kernel;
     switch (h->mode) {
-    case ZMC_FP64: return eval_kernel_fp64(h->integrand);
-    case ZMC_FP32_FP64ACC: return eval_kernel_fp32_fp64acc(h->integrand);
-    default: return eval_kernel_fp32_kahan(h->integrand);
+    case ZMC_FP64: return eval_kernel_fp64(h->integrand, h->dim);
+    case ZMC_FP32_FP64ACC: return eval_kernel_fp32_fp64acc(h->integrand, h->dim);
+    default: return eval_kernel_fp32_kahan(h->integrand, h->dim);
     }
 }
 
@@ -533,13 +533,13 @@ int finish_result(zmc_ctx* h, zmc_result* out) {
 
 // Device tables and per-level graphs of the last batch, reused while the
 // same handles (same buffers, precision and depth) come back.
-// Integrals of a batch that share a sampling kernel (same integrand): a
-// contiguous range of the device table.
+// Integrals of a batch that share a sampling kernel (same integrand, dimension
+// in 1..8 or 9..16): a contiguous range of the device table.
 struct BatchGroup {
     const void* kernel;
     int start, count, grid;
 };
-constexpr int kMaxBatchGroups = kNumIntegrands;
+constexpr int kMaxBatchGroups = 2 * kNumIntegrands;
 
 struct BatchCache {
     int device = -1, capacity = 0;
@@ -914,14 +914,14 @@ ZMC_API int zmc_integrate_batch(int count, const zmc_handle* hs, void* stream,
         ev[i].parents[1] = h->buf.parents[1];
         ev[i].keys = philox_keys(h->seed);
         ev[i].fn = h->integrand;
-        kern[i] = batch_kernel(mode, ev[i].fn);
+        kern[i] = batch_kernel(mode, ev[i].fn, h->dim);
         l1[i] = ipow_sat(h->k, h->dim, INT64_MAX);
         build_desc(h, B.h_desc[i]);
     }
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return ev[a].fn < ev[b].fn;
+        return std::make_pair(ev[a].fn, hs[a]->dim > 8) < std::make_pair(ev[b].fn, hs[b]->dim > 8);
     });
     std::vector<BatchEval> ev_sorted(count);
     std::vector<BatchGroup> groups;

@@ -2,5 +2,5 @@
 #include "batch_kernel.cuh"
 
 namespace zmc {
-const void* batch_kernel_fp32_fp64acc(int fn) { return batch_kernel_for<ZMC_FP32_FP64ACC>(fn); }
+const void* batch_kernel_fp32_fp64acc(int fn, int d) { return batch_kernel_for<ZMC_FP32_FP64ACC>(fn, d); }
 }  // namespace zmc

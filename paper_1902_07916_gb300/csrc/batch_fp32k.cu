@@ -2,5 +2,5 @@
 #include "batch_kernel.cuh"
 
 namespace zmc {
-const void* batch_kernel_fp32_kahan(int fn) { return batch_kernel_for<ZMC_FP32_KAHAN>(fn); }
+const void* batch_kernel_fp32_kahan(int fn, int d) { return batch_kernel_for<ZMC_FP32_KAHAN>(fn, d); }
 }  // namespace zmc

@@ -2,5 +2,5 @@
 #include "batch_kernel.cuh"
 
 namespace zmc {
-const void* batch_kernel_fp64(int fn) { return batch_kernel_for<ZMC_FP64>(fn); }
+const void* batch_kernel_fp64(int fn, int d) { return batch_kernel_for<ZMC_FP64>(fn, d); }
 }  // namespace zmc

@@ -1,5 +1,5 @@
 // Batched sampling kernel (kernel (a) over many integrals).  One persistent
-// kernel per integrand group of a batch: its warps pop work
+// kernel per group of a batch (same integrand, dimension in 1..8 or 9..16): its warps pop work
 // units of the group's integrals from an atomic queue, find the unit's
 // integral by binary search in the group's prefix sums and run the unit
 // exactly as the single-integral kernel would (same unit decomposition, same
@@ -21,7 +21,7 @@ template <int MODE>
 constexpr int batch_min_blocks() { return MODE == ZMC_FP64 ? eval_min_blocks<MODE>() : 3; }
 static_assert(kBatchThreads == kEvalMaxThreads, "shared slices are sized for kEvalMaxThreads");
 
-template <int MODE, int FN>
+template <int MODE, int FN, bool HI>
 __global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<MODE>())
 zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
                const int64_t* __restrict__ offsets, unsigned long long* head) {
@@ -67,12 +67,18 @@ zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
         sample_unit_fold<MODE, FN, DD>(acc, keys, sc, wc, wp, wcst, start, un.g0, un.g1, \
                                              plan.ngroups - 1, plan.tail);                     \
         break;
-        switch (D.d) {
-            ZMC_BATCH_CASE(1) ZMC_BATCH_CASE(2) ZMC_BATCH_CASE(3) ZMC_BATCH_CASE(4)
-            ZMC_BATCH_CASE(5) ZMC_BATCH_CASE(6) ZMC_BATCH_CASE(7) ZMC_BATCH_CASE(8)
-            ZMC_BATCH_CASE(9) ZMC_BATCH_CASE(10) ZMC_BATCH_CASE(11) ZMC_BATCH_CASE(12)
-            ZMC_BATCH_CASE(13) ZMC_BATCH_CASE(14) ZMC_BATCH_CASE(15) ZMC_BATCH_CASE(16)
-            default: break;
+        if constexpr (HI) {
+            switch (D.d) {
+                ZMC_BATCH_CASE(9) ZMC_BATCH_CASE(10) ZMC_BATCH_CASE(11) ZMC_BATCH_CASE(12)
+                ZMC_BATCH_CASE(13) ZMC_BATCH_CASE(14) ZMC_BATCH_CASE(15) ZMC_BATCH_CASE(16)
+                default: break;
+            }
+        } else {
+            switch (D.d) {
+                ZMC_BATCH_CASE(1) ZMC_BATCH_CASE(2) ZMC_BATCH_CASE(3) ZMC_BATCH_CASE(4)
+                ZMC_BATCH_CASE(5) ZMC_BATCH_CASE(6) ZMC_BATCH_CASE(7) ZMC_BATCH_CASE(8)
+                default: break;
+            }
         }
 #undef ZMC_BATCH_CASE
         acc.reduce_store(it.sums + local);
@@ -81,19 +87,23 @@ zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
 }
 
 // One mode's batched instantiations, indexed like eval_kernel_for().
-template <int MODE>
-inline const void* batch_kernel_for(int fn) {
+template <int MODE, bool HI>
+inline const void* batch_kernel_range(int fn) {
     switch (fn) {
-    case kConstant: return (const void*)zmc_batch_eval<MODE, kConstant>;
-    case kLinear: return (const void*)zmc_batch_eval<MODE, kLinear>;
-    case kSinSum: return (const void*)zmc_batch_eval<MODE, kSinSum>;
-    case kGaussNorm: return (const void*)zmc_batch_eval<MODE, kGaussNorm>;
-    case kGenzOsc: return (const void*)zmc_batch_eval<MODE, kGenzOsc>;
-    case kGenzProdPeak: return (const void*)zmc_batch_eval<MODE, kGenzProdPeak>;
-    case kGenzGauss: return (const void*)zmc_batch_eval<MODE, kGenzGauss>;
-    case kGenzCorner: return (const void*)zmc_batch_eval<MODE, kGenzCorner>;
+    case kConstant: return (const void*)zmc_batch_eval<MODE, kConstant, HI>;
+    case kLinear: return (const void*)zmc_batch_eval<MODE, kLinear, HI>;
+    case kSinSum: return (const void*)zmc_batch_eval<MODE, kSinSum, HI>;
+    case kGaussNorm: return (const void*)zmc_batch_eval<MODE, kGaussNorm, HI>;
+    case kGenzOsc: return (const void*)zmc_batch_eval<MODE, kGenzOsc, HI>;
+    case kGenzProdPeak: return (const void*)zmc_batch_eval<MODE, kGenzProdPeak, HI>;
+    case kGenzGauss: return (const void*)zmc_batch_eval<MODE, kGenzGauss, HI>;
+    case kGenzCorner: return (const void*)zmc_batch_eval<MODE, kGenzCorner, HI>;
     default: return nullptr;
     }
+}
+template <int MODE>
+inline const void* batch_kernel_for(int fn, int d) {
+    return d > 8 ? batch_kernel_range<MODE, true>(fn) : batch_kernel_range<MODE, false>(fn);
 }
 
 }  // namespace zmc

@@ -2,5 +2,5 @@
 #include "eval_kernel.cuh"
 
 namespace zmc {
-const void* eval_kernel_fp64(int fn) { return eval_kernel_for<ZMC_FP64>(fn); }
+const void* eval_kernel_fp64(int fn, int d) { return eval_kernel_for<ZMC_FP64>(fn, d); }
 }  // namespace zmc

@@ -44,8 +44,10 @@ constexpr int kEvalMaxWarps = kEvalMaxThreads / 32;
 // registers at 64 (FP32 modes) and 85 (FP64, whose values take two).
 template <int MODE>
 constexpr int eval_min_blocks() { return MODE == ZMC_FP64 ? 3 : 4; }
-// Philox chains of successive dimensions in flight per lane.
-constexpr int kDimUnroll = 8;
+// The dimension loop of a point group (group_values) is unrolled 8-way,
+// which covers d <= 8 completely; for d = 9..16 the FP32 modes unroll it
+// completely, since the remainder iteration of an 8-way unroll cost 2-4%.
+// FP64 keeps 8: its library exp and sin would spill under a full unroll.
 constexpr int kFlushGroups = 16;  // groups per FP32 partial sum (MODE 1)
 
 template <int MODE>
@@ -391,8 +393,7 @@ __device__ __forceinline__ void group_values(
     R a[G];
 #pragma unroll
     for (int p = 0; p < G; ++p) a[p] = start;
-#pragma unroll kDimUnroll
-    for (int i = 0; i < nd; ++i) {
+    auto dimension = [&](int i) {
         const uint4 w = philox_from_product(keys, sc, (uint32_t)(P >> 32), (uint32_t)P);
         P += kPhiloxMulA;
         const R2 ab = w_coef[i];
@@ -401,6 +402,13 @@ __device__ __forceinline__ void group_values(
         block_points<MODE>(w, v);
 #pragma unroll
         for (int p = 0; p < G; ++p) a[p] = F::fold(a[p], v[p], ab.x, ab.y, pb);
+    };
+    if constexpr (MODE != ZMC_FP64 && DIM > 8) {
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) dimension(i);
+    } else {
+#pragma unroll 8
+        for (int i = 0; i < nd; ++i) dimension(i);
     }
     if constexpr (log_domain<MODE, FN>()) {
 #pragma unroll
@@ -447,7 +455,8 @@ __device__ __forceinline__ void sample_unit_fold(
     }
 }
 
-template <int MODE, int FN>
+// One kernel per dimension DIM: each holds only the sample loop its d needs.
+template <int MODE, int FN, int DIM>
 __global__ void __launch_bounds__(kEvalMaxThreads, eval_min_blocks<MODE>())
 zmc_eval_reduce(const Desc* __restrict__ desc, State* st,
                 const uint32_t* __restrict__ parents, double2* __restrict__ partial,
@@ -476,19 +485,8 @@ zmc_eval_reduce(const Desc* __restrict__ desc, State* st,
         const R start = fold_setup<MODE, FN>(D, level, un.q, parents, s_coef[warp], s_term[warp]);
         const StreamConst sc = stream_const(keys, un.t, (uint32_t)un.q, (uint32_t)level);
         SumsFor<MODE, FN> acc(slot, value_scale<MODE, FN>(D));
-#define ZMC_FOLD_CASE(DD)                                                                      \
-    case DD:                                                                                   \
-        sample_unit_fold<MODE, FN, DD>(acc, keys, sc, s_coef[warp], s_pb, s_c, start,    \
-                                             un.g0, un.g1, plan.ngroups - 1, plan.tail);       \
-        break;
-        switch (d) {
-            ZMC_FOLD_CASE(1) ZMC_FOLD_CASE(2) ZMC_FOLD_CASE(3) ZMC_FOLD_CASE(4)
-            ZMC_FOLD_CASE(5) ZMC_FOLD_CASE(6) ZMC_FOLD_CASE(7) ZMC_FOLD_CASE(8)
-            ZMC_FOLD_CASE(9) ZMC_FOLD_CASE(10) ZMC_FOLD_CASE(11) ZMC_FOLD_CASE(12)
-            ZMC_FOLD_CASE(13) ZMC_FOLD_CASE(14) ZMC_FOLD_CASE(15) ZMC_FOLD_CASE(16)
-            default: break;
-        }
-#undef ZMC_FOLD_CASE
+        sample_unit_fold<MODE, FN, DIM>(acc, keys, sc, s_coef[warp], s_pb, s_c, start, un.g0,
+                                        un.g1, plan.ngroups - 1, plan.tail);
         acc.reduce_store(partial + u);
         __syncwarp();   // the warp's coefficient slice is rewritten by the next unit
     }
@@ -576,18 +574,40 @@ __device__ __forceinline__ void eval_expr_body(const Desc* __restrict__ desc,
 }
 
 #ifndef __CUDACC_RTC__
-// One mode's registry instantiations, indexed by integrand id.
+// One mode's registry instantiations, indexed by integrand id and dimension.
+template <int MODE, int FN>
+inline const void* eval_kernel_dim(int d) {
+    switch (d) {
+    case 1: return (const void*)zmc_eval_reduce<MODE, FN, 1>;
+    case 2: return (const void*)zmc_eval_reduce<MODE, FN, 2>;
+    case 3: return (const void*)zmc_eval_reduce<MODE, FN, 3>;
+    case 4: return (const void*)zmc_eval_reduce<MODE, FN, 4>;
+    case 5: return (const void*)zmc_eval_reduce<MODE, FN, 5>;
+    case 6: return (const void*)zmc_eval_reduce<MODE, FN, 6>;
+    case 7: return (const void*)zmc_eval_reduce<MODE, FN, 7>;
+    case 8: return (const void*)zmc_eval_reduce<MODE, FN, 8>;
+    case 9: return (const void*)zmc_eval_reduce<MODE, FN, 9>;
+    case 10: return (const void*)zmc_eval_reduce<MODE, FN, 10>;
+    case 11: return (const void*)zmc_eval_reduce<MODE, FN, 11>;
+    case 12: return (const void*)zmc_eval_reduce<MODE, FN, 12>;
+    case 13: return (const void*)zmc_eval_reduce<MODE, FN, 13>;
+    case 14: return (const void*)zmc_eval_reduce<MODE, FN, 14>;
+    case 15: return (const void*)zmc_eval_reduce<MODE, FN, 15>;
+    case 16: return (const void*)zmc_eval_reduce<MODE, FN, 16>;
+    default: return nullptr;
+    }
+}
 template <int MODE>
-inline const void* eval_kernel_for(int fn) {
+inline const void* eval_kernel_for(int fn, int d) {
     switch (fn) {
-    case kConstant: return (const void*)zmc_eval_reduce<MODE, kConstant>;
-    case kLinear: return (const void*)zmc_eval_reduce<MODE, kLinear>;
-    case kSinSum: return (const void*)zmc_eval_reduce<MODE, kSinSum>;
-    case kGaussNorm: return (const void*)zmc_eval_reduce<MODE, kGaussNorm>;
-    case kGenzOsc: return (const void*)zmc_eval_reduce<MODE, kGenzOsc>;
-    case kGenzProdPeak: return (const void*)zmc_eval_reduce<MODE, kGenzProdPeak>;
-    case kGenzGauss: return (const void*)zmc_eval_reduce<MODE, kGenzGauss>;
-    case kGenzCorner: return (const void*)zmc_eval_reduce<MODE, kGenzCorner>;
+    case kConstant: return eval_kernel_dim<MODE, kConstant>(d);
+    case kLinear: return eval_kernel_dim<MODE, kLinear>(d);
+    case kSinSum: return eval_kernel_dim<MODE, kSinSum>(d);
+    case kGaussNorm: return eval_kernel_dim<MODE, kGaussNorm>(d);
+    case kGenzOsc: return eval_kernel_dim<MODE, kGenzOsc>(d);
+    case kGenzProdPeak: return eval_kernel_dim<MODE, kGenzProdPeak>(d);
+    case kGenzGauss: return eval_kernel_dim<MODE, kGenzGauss>(d);
+    case kGenzCorner: return eval_kernel_dim<MODE, kGenzCorner>(d);
     default: return nullptr;
     }
 }

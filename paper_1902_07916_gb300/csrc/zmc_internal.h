@@ -74,9 +74,9 @@ struct BatchEval {
 // device arrays of `count` entries; row y of each selection grid works on
 // integral y.
 // Batched sampling kernels of one mode by integrand (eval_fp*.cu).
-const void* batch_kernel_fp64(int fn);
-const void* batch_kernel_fp32_fp64acc(int fn);
-const void* batch_kernel_fp32_kahan(int fn);
+const void* batch_kernel_fp64(int fn, int d);
+const void* batch_kernel_fp32_fp64acc(int fn, int d);
+const void* batch_kernel_fp32_kahan(int fn, int d);
 // Plan + sampling kernel of one group of `count` integrals (same integrand):
 // `offsets` has count + 1 entries, `head` is the group's queue counter.
 cudaError_t launch_batch_level(const BatchEval* items, int count, int level, int64_t* offsets,
