@@ -225,8 +225,8 @@ def algorithmic_bytes_per_launch(cells_per_level, n, trials, fp64):
 # kernel's sources it was taken on (profiles/zmc_eval_reduce_sin6d_traffic.md).
 TRAFFIC_CAPTURE = {
     "workload": "sin6d", "fp64": False,
-    "bytes_per_launch": (70912 + 0 + 10710016 + 170334976) / 2,
-    "sources_sha256": "d93fbc690bb856550d4dcf8f44e5e9563b3bda61e3ab373b86c91b795c7c445c",
+    "bytes_per_launch": (32768 + 0 + 10272256 + 171017984) / 2,
+    "sources_sha256": "ac58c981a9814279f2355e0925985ffea10837ad9e03a35a64b51fb0917fccf2",
 }
 KERNEL_SOURCES = ["eval_kernel.cuh", "zmc_device.cuh", "zmc_layout.h", "eval_fp32.cu"]
 
