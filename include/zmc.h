@@ -9,7 +9,7 @@
  * deviation of all the level's spreads are split again into k^d children, down
  * to a maximal depth; the accepted cells' means are summed into the value and
  * their spreads into the error.  Random numbers are made where they are used
- * (Sec. 2.2, "produce-at-calculation"), by Philox4x32-10.
+ * (Sec. 2.2), by Philox4x32-10.
  *
  * Conventions for every call:
  *  - Return value: ZMC_OK (0) or one of the ZMC_ERR_* codes below.  On

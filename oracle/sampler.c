@@ -14,8 +14,8 @@
  * standard deviation, threshold, selection, re-splitting, combination) lives
  * in zmc_oracle.py.
  *
- * Random numbers are made at the point of use (Sec. 2.2, "produce-at-
- * calculation"); the paper names no generator, so the stream is defined here
+ * Random numbers are made at the point of use (Sec. 2.2); the paper names no
+ * generator, so the stream is defined here
  * as Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
  * easy as 1, 2, 3", SC'11) with
  *     key     = (seed mod 2^32, seed div 2^32)

@@ -24,7 +24,7 @@ The method (ZMCintegral, arXiv 1902.07916, Sec. 2.1 and Fig. 1):
 Readings of points the paper leaves open (each is also listed with the design
 notes of the repository):
 
-* k is per dimension (the experiments give "sub-domains in one dimension").
+* k is per dimension (the experiments of Sec. 3 state their counts per dimension).
 * Cells are numbered row-major with dimension 0 fastest; children of the
   r-th flagged parent (in work-list order) take slots r*k^d + digit, where
   digit = sum_i digit_i k^i and the child's lattice coordinate is
@@ -32,7 +32,7 @@ notes of the repository):
 * Per-cell spread: sample standard deviation over trials (ddof 1).
 * Threshold: theta_L = mu_L + m * sigma_L with mu_L, sigma_L the mean and
   population standard deviation (ddof 0) of the level's cell spreads
-  ("larger than 5 sigma" in Sec. 3.1 read as mu + 5 sigma).  A cell is flagged
+  (the five-sigma criterion of Sec. 3.1 read as mu + 5 sigma).  A cell is flagged
   when its spread is strictly larger than theta_L, and never at the last level.
 * Error: std = sqrt(sum over accepted cells of s_c^2 / trials), i.e. the
   standard errors of the accepted cell means added in quadrature.
