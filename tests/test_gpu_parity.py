@@ -155,6 +155,14 @@ FP32_CASES = [
      None),
     (W("prodpeak3", "genz_prodpeak", 3, 0.0, 1.0, 3, 257, 6, 2, 1.0, 4,
        [5.0, 7.0, 2.0, 0.3, 0.5, 0.7]), None),
+    # the high dimensions have their own (fully unrolled) sample loops
+    (W("osc10", "genz_osc", 10, 0.0, 1.0, 2, 96, 4, 2, 1.0, 5,
+       [0.3] + [0.5 + 0.1 * i for i in range(10)]), None),
+    (W("sin12", "sin_sum", 12, 0.0, 1.0, 2, 64, 4, 1, 1.0, 6), None),
+    (W("genzgauss16", "genz_gauss", 16, 0.0, 1.0, 2, 16, 3, 1, 1.0, 7,
+       [0.8] * 16 + [0.4 + 0.01 * i for i in range(16)]), None),
+    (W("linear9", "linear", 9, -1.0, 2.0, 3, 41, 4, 1, 1.0, 8,
+       [0.5] + [0.2 * i - 0.7 for i in range(9)]), None),
 ]
 
 
