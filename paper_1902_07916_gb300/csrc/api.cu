@@ -230,7 +230,8 @@ int ensure_device(zmc_ctx* h) {
         {(void**)&b.desc, sizeof(Desc)},
         {(void**)&b.state, sizeof(State)},
         // partial sums of the sampling kernel's units: a level with `tiles`
-        // tiles has at most tiles + kTargetUnits units (see unit_chunks)
+        // tiles has at most tiles + kTargetUnits unit slots (see unit_chunks;
+        // a lane-tile unit writes one slot per tile)
         {(void**)&b.sums, sizeof(double2) * ((size_t)cap * h->T + (size_t)kTargetUnits)},
         {(void**)&b.cell_stats, sizeof(double2) * (size_t)cap},
         {(void**)&b.parents[0], sizeof(uint32_t) * (size_t)cap_par * h->dim},
@@ -416,7 +417,8 @@ EvalShape eval_shape(zmc_ctx* h, int level, Tuned t) {
     if (level == 1) {
         // no more CTAs than level 1 has units for their warps
         const int64_t tiles = ipow_sat(h->k, h->dim, INT64_MAX) * h->T;
-        const int64_t units = tiles * unit_chunks(tiles, groups_of(h->n, h->mode));
+        const int64_t units =
+            level_units(tiles, groups_of(h->n, h->mode), h->integrand != kExpression);
         grid = std::min(grid, (units + t.threads / 32 - 1) / (t.threads / 32));
     }
     sh.grid = (int)std::max<int64_t>(grid, 1);

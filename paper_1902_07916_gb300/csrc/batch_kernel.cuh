@@ -32,6 +32,7 @@ zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
     __shared__ R s_pb[kEvalMaxWarps][ZMC_MAX_DIM];
     __shared__ R s_c[kEvalMaxWarps][4];
     __shared__ double2 s_acc[MODE == ZMC_FP32_FP64ACC ? kBatchThreads : 1];
+    __shared__ R s_lane_beta[kEvalMaxWarps][(HI ? 16 : 8) * 32];   // lane tiles' betas
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t total = offsets[count];
@@ -55,10 +56,34 @@ zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
         const Desc& D = *it.desc;
         const UnitPlan plan = unit_plan<MODE>(D, it.st->cells[level]);
         const int64_t local = u - offsets[lo];
-        const Unit un = unit_of(plan, local);
         if (lane < D.d) wp[lane] = (R)D.pb[lane];
         if (lane < 4) wcst[lane] = (R)D.c[lane];
         const PhiloxKeys keys = it.keys;
+        if (plan.lane_tiles) {
+            __syncwarp();
+#define ZMC_LANE_CASE(DD)                                                                     \
+    case DD:                                                                                  \
+        lane_tile_unit<MODE, FN, DD>(D, level, plan, local, it.parents[level & 1], keys, wc,  \
+                                     s_lane_beta[warp], wp, wcst, slot, it.sums);             \
+        break;
+            if constexpr (HI) {
+                switch (D.d) {
+                    ZMC_LANE_CASE(9) ZMC_LANE_CASE(10) ZMC_LANE_CASE(11) ZMC_LANE_CASE(12)
+                    ZMC_LANE_CASE(13) ZMC_LANE_CASE(14) ZMC_LANE_CASE(15) ZMC_LANE_CASE(16)
+                    default: break;
+                }
+            } else {
+                switch (D.d) {
+                    ZMC_LANE_CASE(1) ZMC_LANE_CASE(2) ZMC_LANE_CASE(3) ZMC_LANE_CASE(4)
+                    ZMC_LANE_CASE(5) ZMC_LANE_CASE(6) ZMC_LANE_CASE(7) ZMC_LANE_CASE(8)
+                    default: break;
+                }
+            }
+#undef ZMC_LANE_CASE
+            __syncwarp();   // the warp's shared slices are rewritten by its next unit
+            continue;
+        }
+        const Unit un = unit_of(plan, local);
         const R start = fold_setup<MODE, FN>(D, level, un.q, it.parents[level & 1], wc, wt);
         const StreamConst sc = stream_const(keys, un.t, (uint32_t)un.q, (uint32_t)level);
         SumsFor<MODE, FN> acc(slot, value_scale<MODE, FN>(D));

@@ -154,6 +154,13 @@ struct LaneSums {
         }
         if ((threadIdx.x & 31) == 0) *out = make_double2(a, b);
     }
+
+    // This lane's own sums (a tile run by one lane): no warp reduction.
+    __device__ __forceinline__ void store_lane(double2* out) {
+        if constexpr (MODE == ZMC_FP64) *out = make_double2(S1d, S2d);
+        else if constexpr (MODE == ZMC_FP32_FP64ACC) *out = *slot;
+        else *out = make_double2((double)s1 + (double)e1, (double)s2 + (double)e2);
+    }
 };
 
 // FP32 modes for integrands of the form C * 2^t (the Gaussians): the group
@@ -255,6 +262,20 @@ struct LogLaneSums {
         }
         if ((threadIdx.x & 31) == 0) *out = make_double2(a * scale, b * (scale * scale));
     }
+
+    __device__ __forceinline__ void store_lane(double2* out) {
+        double a, b;
+        if constexpr (MODE == ZMC_FP32_FP64ACC) {
+            const double2 v = *slot;
+            a = v.x;
+            b = v.y;
+        } else {
+            const int ke = exp_of(k);
+            a = (k == neg_inf()) ? 0.0 : ldexp((double)s1 + (double)e1, ke);
+            b = (k == neg_inf()) ? 0.0 : ldexp((double)s2 + (double)e2, 2 * ke);
+        }
+        *out = make_double2(a * scale, b * (scale * scale));
+    }
 };
 
 // The lane accumulator of integrand FN in mode MODE.
@@ -284,20 +305,23 @@ __device__ __forceinline__ void mask_tail(bool last, uint32_t tail, R (&f)[G], R
 
 // Decomposition of the level's work into units (see unit_chunks()).
 struct UnitPlan {
-    int64_t units, chunks;
+    int64_t units, chunks, tiles;
     uint32_t ngroups, tail;
     int T;
+    bool lane_tiles;   // a unit is 32 tiles, one per lane (see kLaneTileGroups)
 };
 
 template <int MODE>
-__device__ __forceinline__ UnitPlan unit_plan(const Desc& D, int64_t C) {
+__device__ __forceinline__ UnitPlan unit_plan(const Desc& D, int64_t C,
+                                              bool allow_lane_tiles = true) {
     UnitPlan p;
     p.T = D.T;
     p.ngroups = (uint32_t)groups_of(D.n, MODE);             // < 2^32: n * d < 2^34
     p.tail = (uint32_t)(D.n - (int64_t)kGroup<MODE> * (int64_t)(p.ngroups - 1));
-    const int64_t tiles = C * D.T;
-    p.chunks = unit_chunks(tiles, p.ngroups);
-    p.units = tiles * p.chunks;
+    p.tiles = C * D.T;
+    p.lane_tiles = allow_lane_tiles && lane_tiles(p.ngroups);
+    p.chunks = unit_chunks(p.tiles, p.ngroups);          // 1 for lane tiles
+    p.units = level_units(p.tiles, p.ngroups, allow_lane_tiles);
     return p;
 }
 
@@ -376,14 +400,34 @@ __device__ __forceinline__ typename ModeTraits<MODE>::R fold_setup(
     return (R)a0;
 }
 
+// Where group_values finds dimension i's fold coefficients (alpha, beta):
+// one pair per dimension for the whole warp (a unit of one tile), or the
+// warp's alpha with this lane's own beta (lane tiles: beta carries the
+// cell's position, alpha only the level's width).
+template <typename R, typename R2>
+struct WarpCoef {
+    const R2* ab;
+    __device__ __forceinline__ R2 operator()(int i) const { return ab[i]; }
+};
+template <typename R, typename R2>
+struct LaneCoef {
+    const R2* ab;     // [d], the warp's (alpha, unused)
+    const R* beta;    // [d * 32], this lane's at beta[i * 32]
+    __device__ __forceinline__ R2 operator()(int i) const {
+        R2 r = ab[i];
+        r.y = beta[i * 32];
+        return r;
+    }
+};
+
 // The values of one point group (G points) of a registry integrand: the
 // Philox block of every dimension (round 1's product A * c0 given as P, the
 // 64-bit product for dimension 0), each folded into the G running sums, then
 // the finishing function.
-template <int MODE, int FN, int DIM>
+template <int MODE, int FN, int DIM, class Coef>
 __device__ __forceinline__ void group_values(
-    const PhiloxKeys& keys, const StreamConst& sc,
-    const typename ModeTraits<MODE>::R2* w_coef, const typename ModeTraits<MODE>::R* s_pb,
+    const PhiloxKeys& keys, const StreamConst& sc, const Coef& coef,
+    const typename ModeTraits<MODE>::R* s_pb,
     const typename ModeTraits<MODE>::R* s_c, typename ModeTraits<MODE>::R start, uint64_t P,
     int nd, typename ModeTraits<MODE>::R (&f)[kGroup<MODE>]) {
     using R = typename ModeTraits<MODE>::R;
@@ -396,7 +440,7 @@ __device__ __forceinline__ void group_values(
     auto dimension = [&](int i) {
         const uint4 w = philox_from_product(keys, sc, (uint32_t)(P >> 32), (uint32_t)P);
         P += kPhiloxMulA;
-        const R2 ab = w_coef[i];
+        const R2 ab = coef(i);
         const R pb = s_pb[i];
         R v[G];
         block_points<MODE>(w, v);
@@ -432,6 +476,7 @@ __device__ __forceinline__ void sample_unit_fold(
     const typename ModeTraits<MODE>::R* s_c, typename ModeTraits<MODE>::R start,
     uint32_t g0, uint32_t g1, uint32_t last_group, uint32_t tail, int dim_rt = 0) {
     using R = typename ModeTraits<MODE>::R;
+    using R2 = typename ModeTraits<MODE>::R2;
     const int nd = DIM > 0 ? DIM : dim_rt;
     const uint64_t step = (uint64_t)kPhiloxMulA * (uint64_t)(32 * nd);
     uint32_t g = g0 + (threadIdx.x & 31);
@@ -441,18 +486,75 @@ __device__ __forceinline__ void sample_unit_fold(
     while (g < full_end) {
         for (int j = 0; j < kFlushGroups && g < full_end; ++j, g += 32, Pg += step) {
             R f[G];
-            group_values<MODE, FN, DIM>(keys, sc, w_coef, s_pb, s_c, start, Pg, nd, f);
+            group_values<MODE, FN, DIM>(keys, sc, WarpCoef<R, R2>{w_coef}, s_pb, s_c, start, Pg, nd, f);
             acc.add(f);
         }
         acc.flush();
     }
     if (g == last_group && g < g1) {
         R f[G];
-        group_values<MODE, FN, DIM>(keys, sc, w_coef, s_pb, s_c, start, Pg, nd, f);
+        group_values<MODE, FN, DIM>(keys, sc, WarpCoef<R, R2>{w_coef}, s_pb, s_c, start, Pg, nd, f);
         mask_tail(true, tail, f, log_domain<MODE, FN>() ? R(neg_inf()) : R(0));
         acc.add(f);
         acc.flush();
     }
+}
+
+// A unit of 32 small tiles, one per lane (plan.lane_tiles): each lane sets up
+// its own cell (the same FP64 fold coefficients and start value as
+// fold_setup), runs all of its tile's groups in order and writes the tile's
+// sums itself -- no warp reduction.  The level's alpha per dimension goes to
+// w_coef[i].x (equal for every lane, lanes < d write it), the lane's beta to
+// lane_beta[i * 32 + lane].  Ends with the warp converged.
+template <int MODE, int FN, int DIM>
+__device__ __forceinline__ void lane_tile_unit(
+    const Desc& D, int level, const UnitPlan& plan, int64_t u, const uint32_t* parents,
+    const PhiloxKeys& keys, typename ModeTraits<MODE>::R2* w_coef,
+    typename ModeTraits<MODE>::R* lane_beta,
+    const typename ModeTraits<MODE>::R* s_pb, const typename ModeTraits<MODE>::R* s_c,
+    double2* slot, double2* partial) {
+    using R = typename ModeTraits<MODE>::R;
+    using R2 = typename ModeTraits<MODE>::R2;
+    using F = Fn<FN, R>;
+    constexpr int G = kGroup<MODE>;
+    const int lane = threadIdx.x & 31;
+    const int64_t tile = u * 32 + lane;
+    const bool active = tile < plan.tiles;
+    const int64_t q = active ? tile / plan.T : 0;
+    const uint32_t t = active ? (uint32_t)(tile - q * plan.T) : 0u;
+    double a0 = (double)F::init();
+    for (int i = 0; i < DIM; ++i) {
+        const double w = D.width[level][i];
+        const double b = active ? cell_shift<MODE>(D, level, q, i, parents, w) : 0.0;
+        const Prep p = F::prep(w, b, D.pa[i], D.pb[i]);
+        if (lane == i) w_coef[i].x = (R)p.alpha;
+        lane_beta[i * 32 + lane] = (R)p.beta;
+        a0 += p.term;
+    }
+    __syncwarp();
+    if (!active) return;
+    const R start = (R)a0;
+    const LaneCoef<R, R2> coef{w_coef, lane_beta + lane};
+    const StreamConst sc = stream_const(keys, t, (uint32_t)q, (uint32_t)level);
+    SumsFor<MODE, FN> acc(slot, value_scale<MODE, FN>(D));
+    const uint64_t step = (uint64_t)kPhiloxMulA * (uint64_t)DIM;
+    const uint32_t last = plan.ngroups - 1;
+    uint64_t Pg = 0;
+    uint32_t g = 0;
+    while (g < last) {
+        for (int j = 0; j < kFlushGroups && g < last; ++j, ++g, Pg += step) {
+            R f[G];
+            group_values<MODE, FN, DIM>(keys, sc, coef, s_pb, s_c, start, Pg, DIM, f);
+            acc.add(f);
+        }
+        acc.flush();
+    }
+    R f[G];
+    group_values<MODE, FN, DIM>(keys, sc, coef, s_pb, s_c, start, Pg, DIM, f);
+    mask_tail(true, plan.tail, f, log_domain<MODE, FN>() ? R(neg_inf()) : R(0));
+    acc.add(f);
+    acc.flush();
+    acc.store_lane(partial + tile);
 }
 
 // One kernel per dimension DIM: each holds only the sample loop its d needs.
@@ -467,6 +569,7 @@ zmc_eval_reduce(const Desc* __restrict__ desc, State* st,
     __shared__ double s_term[kEvalMaxWarps][ZMC_MAX_DIM];
     __shared__ R s_pb[ZMC_MAX_DIM], s_c[4];
     __shared__ double2 s_acc[MODE == ZMC_FP32_FP64ACC ? kEvalMaxThreads : 1];
+    __shared__ R s_lane_beta[kEvalMaxWarps][DIM * 32];
 
     const Desc& D = *desc;
     const int64_t C = st->cells[level];
@@ -481,6 +584,12 @@ zmc_eval_reduce(const Desc* __restrict__ desc, State* st,
     const UnitQueue queue(st, level);
     double2* slot = &s_acc[MODE == ZMC_FP32_FP64ACC ? tid : 0];
     for (int64_t u = queue.first(); u < plan.units; u = queue.next()) {
+        if (plan.lane_tiles) {
+            lane_tile_unit<MODE, FN, DIM>(D, level, plan, u, parents, keys, s_coef[warp],
+                                          s_lane_beta[warp], s_pb, s_c, slot, partial);
+            __syncwarp();
+            continue;
+        }
         const Unit un = unit_of(plan, u);
         const R start = fold_setup<MODE, FN>(D, level, un.q, parents, s_coef[warp], s_term[warp]);
         const StreamConst sc = stream_const(keys, un.t, (uint32_t)un.q, (uint32_t)level);
@@ -517,7 +626,7 @@ __device__ __forceinline__ void eval_expr_body(const Desc* __restrict__ desc,
     if (tid < 4) s_p[2 * ZMC_MAX_DIM + tid] = (R)D.c[tid];
     __syncthreads();
 
-    const UnitPlan plan = unit_plan<MODE>(D, C);
+    const UnitPlan plan = unit_plan<MODE>(D, C, false);
     const UnitQueue queue(st, level);
     double2* slot = &s_acc[MODE == ZMC_FP32_FP64ACC ? tid : 0];
     R2* wb = s_wb[warp];

@@ -97,4 +97,24 @@ inline int64_t unit_chunks(int64_t tiles, int64_t ngroups) {
     return want < most ? (want < 1 ? 1 : want) : most;
 }
 
+// Tiles of fewer point groups than this run one per lane: a unit is then 32
+// consecutive tiles, each lane one whole tile (a warp's lanes would otherwise
+// idle, and the per-tile set-up and warp reduction would dominate).  The
+// registry kernels use it; expression kernels keep one tile per warp.
+constexpr int64_t kLaneTileGroups = 64;
+
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline bool lane_tiles(int64_t ngroups) { return ngroups < kLaneTileGroups; }
+
+// Work units of a level of `tiles` tiles of `ngroups` groups each.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int64_t level_units(int64_t tiles, int64_t ngroups, bool allow_lane_tiles) {
+    if (allow_lane_tiles && lane_tiles(ngroups)) return (tiles + 31) / 32;
+    return tiles * unit_chunks(tiles, ngroups);
+}
+
 }  // namespace zmc
