@@ -319,7 +319,7 @@ __device__ __forceinline__ UnitPlan unit_plan(const Desc& D, int64_t C,
     p.ngroups = (uint32_t)groups_of(D.n, MODE);             // < 2^32: n * d < 2^34
     p.tail = (uint32_t)(D.n - (int64_t)kGroup<MODE> * (int64_t)(p.ngroups - 1));
     p.tiles = C * D.T;
-    p.lane_tiles = allow_lane_tiles && lane_tiles(p.ngroups);
+    p.lane_tiles = allow_lane_tiles && lane_tiles(p.tiles, p.ngroups);
     p.chunks = unit_chunks(p.tiles, p.ngroups);          // 1 for lane tiles
     p.units = level_units(p.tiles, p.ngroups, allow_lane_tiles);
     return p;

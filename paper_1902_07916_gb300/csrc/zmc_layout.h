@@ -97,23 +97,31 @@ inline int64_t unit_chunks(int64_t tiles, int64_t ngroups) {
     return want < most ? (want < 1 ? 1 : want) : most;
 }
 
-// Tiles of fewer point groups than this run one per lane: a unit is then 32
-// consecutive tiles, each lane one whole tile (a warp's lanes would otherwise
-// idle, and the per-tile set-up and warp reduction would dominate).  The
-// registry kernels use it; expression kernels keep one tile per warp.
+// Lane tiles: a unit of 32 consecutive tiles, each lane one whole tile, in
+// place of one tile per warp (which leaves lanes idle on small tiles and pays
+// a per-tile set-up and FP64 warp reduction).  Taken for tiles of fewer than
+// kLaneTileGroups point groups always, and for tiles of fewer than
+// kMinUnitGroups groups (one unit per tile otherwise) when the level has at
+// least kLaneTileMinTiles tiles, enough units of 32 to keep every warp busy.
+// A function of the level's size and n only.  The registry kernels use it;
+// expression kernels keep one tile per warp.
 constexpr int64_t kLaneTileGroups = 64;
+constexpr int64_t kLaneTileMinTiles = int64_t(1) << 18;
 
 #ifdef __CUDACC__
 __host__ __device__
 #endif
-inline bool lane_tiles(int64_t ngroups) { return ngroups < kLaneTileGroups; }
+inline bool lane_tiles(int64_t tiles, int64_t ngroups) {
+    return ngroups < kLaneTileGroups ||
+           (ngroups < kMinUnitGroups && tiles >= kLaneTileMinTiles);
+}
 
 // Work units of a level of `tiles` tiles of `ngroups` groups each.
 #ifdef __CUDACC__
 __host__ __device__
 #endif
 inline int64_t level_units(int64_t tiles, int64_t ngroups, bool allow_lane_tiles) {
-    if (allow_lane_tiles && lane_tiles(ngroups)) return (tiles + 31) / 32;
+    if (allow_lane_tiles && lane_tiles(tiles, ngroups)) return (tiles + 31) / 32;
     return tiles * unit_chunks(tiles, ngroups);
 }
 

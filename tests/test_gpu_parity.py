@@ -235,3 +235,21 @@ def test_fp32_sine_of_large_arguments(zmc, prec):
     assert res.flagged_per_level == ref.flagged_per_level
     exact = CF.integral(w.integrand, w.lo, w.hi, w.params)
     assert abs(res.value - exact) <= 4 * res.std + 1e-3 * abs(exact), (res.value, exact, res.std)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_fp64acc"])
+def test_lane_tiles_on_a_large_level(zmc, prec):
+    """A level of 373,248 tiles of 320 (FP64) or 256 (FP32) point groups: the
+    sampling kernel runs 32 whole tiles per warp, one per lane, with no warp
+    reduction.  FP64: every sum, statistic and flag against the oracle; FP32:
+    sums against the oracle on the same points, consistent decisions."""
+    w = W("sin6_lanes", "sin_sum", 6, 0.0, 1.0, 6, 1280, 8, 1, 1.0, 12)
+    if prec == "fp64":
+        res, levels = run_gpu(zmc, w, prec)
+        compare_fp64(w, res, levels, run_oracle(w))
+    else:
+        res, levels = run_gpu(zmc, w, prec)
+        ref = run_oracle(w, fp32_uniforms=True)
+        err = np.abs(levels[0]["sums"] - ref.levels[0].sums)
+        assert np.all(err <= sums_tolerance(ref.levels[0].sums, w.n, 2e-5)), float(err.max())
+        check_decisions_consistent(w, levels, res)
