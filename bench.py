@@ -225,8 +225,8 @@ def algorithmic_bytes_per_launch(cells_per_level, n, trials, fp64):
 # kernel's sources it was taken on (profiles/zmc_eval_reduce_sin6d_traffic.md).
 TRAFFIC_CAPTURE = {
     "workload": "sin6d", "fp64": False,
-    "bytes_per_launch": (32768 + 0 + 10272256 + 171017984) / 2,
-    "sources_sha256": "ac58c981a9814279f2355e0925985ffea10837ad9e03a35a64b51fb0917fccf2",
+    "bytes_per_launch": (72704 + 0 + 11275776 + 171680768) / 2,
+    "sources_sha256": "f63636058ea14b2aff5e6a428949623b680fbfc3c240c07751b85c5717758593",
 }
 KERNEL_SOURCES = ["eval_kernel.cuh", "zmc_device.cuh", "zmc_layout.h", "eval_fp32.cu"]
 
