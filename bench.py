@@ -226,17 +226,24 @@ def algorithmic_bytes_per_launch(cells_per_level, n, trials, fp64):
 TRAFFIC_CAPTURE = {
     "workload": "sin6d", "fp64": False,
     "bytes_per_launch": (72704 + 0 + 11275776 + 171680768) / 2,
-    "sources_sha256": "f63636058ea14b2aff5e6a428949623b680fbfc3c240c07751b85c5717758593",
+    "sources_sha256": "478a7e8ac92d7aea7367a779c70d0c2ef9ca931af83dc630af083a61a4f75f38",
 }
 KERNEL_SOURCES = ["eval_kernel.cuh", "zmc_device.cuh", "zmc_layout.h", "eval_fp32.cu"]
 
 
 def kernel_sources_sha256() -> str:
+    """SHA-256 of the kernel's sources with comments and blank lines removed,
+    so that the capture stays valid across comment edits and no longer."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1902_07916_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1902_07916_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        lines = [ln.rstrip() for ln in text.splitlines() if ln.strip()]
+        h.update("\n".join(lines).encode())
     return h.hexdigest()
 
 

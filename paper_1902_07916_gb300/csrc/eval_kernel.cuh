@@ -1,10 +1,11 @@
 // Kernel (a): the fused sample-generate / evaluate / reduce kernel.
 //
-// Work is cut into units: a unit is a contiguous range of the point groups
-// of one (cell, trial) tile (unit_chunks() units per tile).  Every warp walks
-// the level's units persistently and independently (unit += number of warps
-// in the grid); the level's cell count is read from device memory, so the
-// host never needs it.  Per unit:
+// Work is cut into units.  Usually a unit is a contiguous range of the point
+// groups of one (cell, trial) tile (unit_chunks() units per tile); for small
+// tiles on large levels (lane_tiles()) a unit is 32 consecutive whole tiles,
+// one per lane.  Every warp takes its first unit by its index and the rest
+// from the level's atomic counter; the level's cell count is read from device
+// memory, so the host never needs it.  Per unit of one tile:
 //   1. lanes < d decode the cell's lattice coordinates from the slot index
 //      (level 1: base-k digits; deeper: parent coordinates * k + child digit)
 //      and fold the cell's geometry into the integrand's per-dimension
@@ -17,21 +18,24 @@
 //   3. f and f^2 are summed per lane, then across the warp with shuffles, and
 //      lane 0 writes the unit's (S1, S2) to the partial-sum array.  The
 //      statistics kernel adds a tile's units in a fixed order.
+// A lane-tile unit does 1-3 per lane for its own tile and writes the tile's
+// sums without a warp reduction (lane_tile_unit).
 // No CTA-wide barrier is involved, and the summation order depends on n, d
 // and the level's size only -- not on the CTA size or grid chosen to run it.
 //
-// The dimension loop is compiled for every d in 1..16 (a switch picks the
-// copy once per unit) and unrolled, so the Philox chains of successive
-// dimensions interleave.  Registry integrands fold each coordinate into G
-// independent accumulators as it is produced; expression integrands
-// (compiled at run time, d fixed) keep the G points' coordinates in
-// registers and evaluate the expression on each.
+// There is one kernel per dimension d in 1..16 and the dimension loop is
+// unrolled, so the Philox chains of successive dimensions interleave.
+// Registry integrands fold each coordinate into G independent accumulators
+// as it is produced; expression integrands (compiled at run time, d fixed)
+// keep the G points' coordinates in registers and evaluate the expression on
+// each.
 //
 // MODE 0: FP64 throughout.  MODE 1: FP32 points and integrand, FP32 partial
 // sums over 16 groups (80 points) flushed into FP64 per-lane sums, FP64 warp
 // reduction.  MODE 2: FP32 points and integrand with TwoSum-compensated
 // per-lane sums and a TwoSum warp reduction; the (sum, error) float pair is
-// widened to FP64 only for the stored result.
+// widened to FP64 only for the stored result.  The Gaussian integrands run
+// in the log2 domain in MODE 1 and 2 (LogLaneSums).
 #pragma once
 
 #include "zmc_device.cuh"
