@@ -163,6 +163,10 @@ FP32_CASES = [
        [0.8] * 16 + [0.4 + 0.01 * i for i in range(16)]), None),
     (W("linear9", "linear", 9, -1.0, 2.0, 3, 41, 4, 1, 1.0, 8,
        [0.5] + [0.2 * i - 0.7 for i in range(9)]), None),
+    # tiles of 64..1023 groups on small levels (one tile per warp)
+    (W("sin6_seg8", "sin_sum", 6, 0.0, 1.0, 4, 640, 8, 1, 1.0, 13), None),
+    (W("genzgauss5_seg16", "genz_gauss", 5, 0.0, 1.0, 5, 600, 8, 1, 1.0, 14,
+       [3.0, 4.0, 5.0, 6.0, 7.0, 0.3, 0.4, 0.5, 0.6, 0.7]), None),
 ]
 
 
