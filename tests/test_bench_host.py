@@ -30,3 +30,20 @@ def test_median_first():
     assert bench.median_first([None, 2, None, 1, 16]) == (16, 4)
     assert bench.median_first([None, 2, None, 1, None]) == (None, None)
     assert bench.median_first([2, 2, 2, 2, 2]) == (2, 2)
+
+
+def test_algorithmic_bytes_of_the_benchmark_step():
+    # sin6d: level 1 has 4096 x 10 tiles of 13108 point groups, cut into
+    # ceil(2^18 / 40960) = 7 units each; level 2 has 1,204,224 x 10 tiles, one
+    # unit each; 16 bytes per unit, averaged over the two launches
+    level1 = 4096 * 10 * 7 * 16
+    level2 = 1204224 * 10 * 16
+    got = bench.algorithmic_bytes_per_launch([4096, 1204224], 1 << 16, 10, False)
+    assert got == (level1 + level2) / 2 == 98631680
+
+
+def test_fp32_flop_counts():
+    assert bench.fp32_flops_per_sample("sin_sum", 6) == 18
+    assert bench.fp32_flops_per_sample("gauss_norm", 9) == 41
+    # corner peak: r^(d+1) by binary powering, e = 9 = 0b1001: 4 squarings, 2 products
+    assert bench.fp32_flops_per_sample("genz_corner", 8) == 2 * 8 + 4 + 2 + 3
