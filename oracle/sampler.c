@@ -8,16 +8,14 @@
  * Plain, slow, obviously correct FP64 C.  It computes, for each requested
  * (cell, trial) pair of one tree level, the direct Monte Carlo sums
  *     S1 = sum_s f(x_s),   S2 = sum_s f(x_s)^2
- * over the n sample points of that trial (Sec. 2.1: "the integral in each
- * hypercube is calculated using the direct Monte Carlo method ... repeated
- * independently by n1 times").  Everything above this step (per-cell mean and
- * standard deviation, threshold, selection, re-splitting, combination) lives
- * in zmc_oracle.py.
+ * over the n sample points of that trial (Sec. 2.1: each cell's integral is a
+ * plain Monte Carlo estimate, repeated over n1 independent trials).  Everything
+ * above this step (per-cell mean and standard deviation, threshold, selection,
+ * re-splitting, combination) lives in zmc_oracle.py.
  *
  * Random numbers are made at the point of use (Sec. 2.2); the paper names no
- * generator, so the stream is defined here
- * as Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
- * easy as 1, 2, 3", SC'11) with
+ * generator, so the stream is defined here as Philox4x32-10 (Salmon, Moraes,
+ * Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11) with
  *     key     = (seed mod 2^32, seed div 2^32)
  *     counter = ((s div G) * d + i,  t,  q,  L)
  * for sample s in [0, n), dimension i in [0, d), trial t, work-list slot q and

@@ -196,6 +196,9 @@ def cell_sums(seed: int, level: int, lo, hi, k: int, n: int, trials: int,
     ``slots`` are the cells' work-list slots q (they select the random
     stream), ``coords`` their lattice coordinates at ``level`` (cells, d).
     """
+    if integrand.startswith("expr:"):
+        return expression_cell_sums(seed, level, lo, hi, k, n, trials, integrand, params,
+                                    slots, coords, fp32_uniforms)
     lib = _load()
     lo = np.ascontiguousarray(lo, dtype=np.float64)
     hi = np.ascontiguousarray(hi, dtype=np.float64)
@@ -215,6 +218,29 @@ def cell_sums(seed: int, level: int, lo, hi, k: int, n: int, trials: int,
         _ptr(out, ctypes.c_double))
     if rc != 0:
         raise ValueError("oracle sampler rejected its arguments")
+    return out
+
+
+def expression_cell_sums(seed: int, level: int, lo, hi, k: int, n: int, trials: int,
+                         expr: str, params, slots, coords, fp32_uniforms=False) -> np.ndarray:
+    """(S1, S2) per (cell, trial) for an expression integrand ("expr:..."):
+    the same stream, points and sample-order sums as the C sampler, with the
+    integrand evaluated by the expression evaluator (expression.py).  For the
+    small cases the tests run (numpy over each tile's points)."""
+    from .expression import Expression
+    e = Expression(expr)
+    lo = np.asarray(lo, dtype=np.float64)
+    width = level_widths(lo, hi, k, level)
+    coords = np.asarray(coords, dtype=np.int64).reshape(-1, lo.size)
+    slots = np.asarray(slots, dtype=np.int64)
+    out = np.zeros((coords.shape[0], trials, 2), dtype=np.float64)
+    for c in range(coords.shape[0]):
+        for t in range(trials):
+            u = stream_uniforms(seed, level, int(slots[c]), t, lo.size, fp32_uniforms, 0, n)
+            x = lo + (coords[c].astype(np.float64) + u) * width     # add, multiply, add
+            f = e.eval(x, params)
+            out[c, t, 0] = np.cumsum(f)[-1]                          # in sample order
+            out[c, t, 1] = np.cumsum(f * f)[-1]
     return out
 
 

@@ -47,6 +47,28 @@ def test_selection_rule_hand_cases(oracle):
     assert oracle.select(o, theta, 1, 2).tolist() == [False] * 7 + [True]
 
 
+def test_margins_hand_cases(oracle):
+    # margin_c = |s_c - theta| / theta: the relative distance of a decision
+    # from a tie, taken against theta (not mu), the same on both sides
+    s = np.array([1.0, 1.0, 3.0, 3.0])
+    mu, _, theta = oracle.threshold(s, 0.5)          # mu = 2, theta = 2.5
+    assert mu == 2.0 and theta == 2.5
+    m = oracle.margins(s, theta)
+    assert m.tolist() == [0.6, 0.6, 0.2, 0.2]        # |1 - 2.5| / 2.5, |3 - 2.5| / 2.5
+    # an exact tie at theta has margin 0
+    assert oracle.margins(np.array([2.5, 0.5]), 2.5).tolist() == [0.0, 0.8]
+    # theta <= 0 (every spread 0): no decision is near a tie
+    assert np.all(np.isinf(oracle.margins(np.zeros(3), 0.0)))
+    # the per-level minimum the oracle reports is that of its own spreads and
+    # threshold, and +inf at the last level (no decision is taken there)
+    r = oracle.integrate(2, [0.0, 0.0], [1.0, 1.0], 3, 40, 4, 2, 0.5, 3, "genz_gauss",
+                         [6.0, 6.0, 0.5, 0.5], keep_levels=True)
+    lv = r.levels[0]
+    expect = float(np.min(np.abs(lv.spread - lv.theta) / lv.theta))
+    assert r.min_margin_per_level[0] == lv.min_margin == expect
+    assert r.levels_run == 2 and math.isinf(r.min_margin_per_level[1])
+
+
 def test_trial_statistics_ddof(oracle):
     sums = np.zeros((2, 3, 2))
     sums[0, :, 0] = [1.0, 2.0, 3.0]
