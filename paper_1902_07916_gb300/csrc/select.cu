@@ -8,8 +8,6 @@
 #include <float.h>
 #include <math.h>
 
-#include <map>
-#include <mutex>
 #include <string>
 
 #include "zmc_device.cuh"
@@ -607,25 +605,17 @@ zmc_level_stats_noalloc_kernel(const double2* __restrict__ sums, int64_t C, int 
 }
 
 namespace {
-std::mutex g_noalloc_mu;
-std::map<int, double*> g_noalloc_addr;   // device -> device address of the scratch
-
-// Once per device, with that device current: the device address of the
-// scratch array (in host code its name is only a host-side stand-in).
-int noalloc_scratch(int dev, double** out, std::string* why) {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    auto it = g_noalloc_addr.find(dev);
-    if (it != g_noalloc_addr.end()) {
-        *out = it->second;
-        return ZMC_OK;
-    }
+// The device address of the scratch array on the current device (in host
+// code its name is only a host-side stand-in).  Looked up on every call, with
+// the caller's device current: the lookup allocates nothing, and a cached
+// address would go stale if the caller reset the device's context.
+int noalloc_scratch(double** out, std::string* why) {
     double* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
     if (e != cudaSuccess) {
         *why = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
         return ZMC_ERR_CUDA;
     }
-    g_noalloc_addr[dev] = p;
     *out = p;
     return ZMC_OK;
 }
@@ -652,16 +642,10 @@ int level_stats_noalloc(const double* sums, int64_t cells, int trials, int64_t n
         g_noalloc_error = "need trials >= 2, n >= 1, finite volume, finite sigma_multiplier >= 0";
         return ZMC_ERR_ARG;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        g_noalloc_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
-        return ZMC_ERR_CUDA;
-    }
     double* scratch = nullptr;
-    if (int rc = noalloc_scratch(dev, &scratch, &g_noalloc_error)) return rc;
+    if (int rc = noalloc_scratch(&scratch, &g_noalloc_error)) return rc;
     // The scratch keeps the previous call's contents: the ticket must start at 0.
-    e = cudaMemsetAsync(scratch + kNoAllocMaxBlocks * 3, 0, sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(scratch + kNoAllocMaxBlocks * 3, 0, sizeof(uint32_t), s);
     if (e == cudaSuccess) {
         const int grid = (int)((cells + kNoAllocCellsPerBlock - 1) / kNoAllocCellsPerBlock);
         zmc_level_stats_noalloc_kernel<<<grid, kSelThreads, 0, s>>>(

@@ -116,3 +116,35 @@ def check_decisions_consistent(w, levels, res):
     assert math.isclose(res.value, math.fsum(acc_mean), rel_tol=1e-12,
                         abs_tol=1e-13 * max(1.0, sum(abs(x) for x in acc_mean)))
     assert math.isclose(res.std, math.sqrt(math.fsum(acc_var)), rel_tol=1e-12)
+
+
+FP32_SUM_RTOL = 2e-5
+# FP32 evaluation moves a spread by about FP32_SUM_RTOL relative: a decision
+# whose oracle margin is below this may legitimately go the other way.
+FP32_DECISION_MARGIN = 1e-3
+
+
+def fp32_levels_against_oracle(w, levels, ref):
+    """Every level's sums against the oracle on the same (FP32-stream) points
+    of the kernel's own cells; the kernel's flags against the oracle's while
+    the two trees agree.  Returns the number of divergent decisions (each
+    within FP32_DECISION_MARGIN of the oracle's threshold)."""
+    coords = level_coords(w, levels)
+    divergent = 0
+    for L, g in enumerate(levels, start=1):
+        if g["cells"] == 0:
+            break
+        sums = O.cell_sums(w.seed, L, w.lo, w.hi, w.k, w.n, w.trials, w.integrand, w.params,
+                           np.arange(g["cells"]), coords[L - 1], fp32_uniforms=True)
+        err = np.abs(g["sums"] - sums)
+        assert np.all(err <= sums_tolerance(sums, w.n, FP32_SUM_RTOL)), (L, float(err.max()))
+        if divergent == 0 and L <= len(ref.levels) and np.array_equal(ref.levels[L - 1].coords,
+                                                                      coords[L - 1]):
+            r = ref.levels[L - 1]
+            flagged = {tuple(c) for c in g["parents_out"].astype(np.int64)}
+            mine = np.array([tuple(c) in flagged for c in coords[L - 1]], dtype=bool)
+            differ = mine != r.flags
+            m = O.margins(r.spread, r.theta)
+            assert np.all(m[differ] < FP32_DECISION_MARGIN), (L, float(m[differ].max()))
+            divergent += int(differ.sum())
+    return divergent

@@ -3,9 +3,10 @@
 FP64 mode: Philox words bit-exact; per-(cell, trial) sums within 1e-12
 relative; identical selection decisions (same flagged cells, same order);
 final value and error within 1e-10 relative.  FP32 modes: per-(cell, trial)
-sums within the FP32 evaluation tolerance of the oracle run on the same
-(23-bit) uniforms, decisions consistent with the kernel's own statistics, and
-the value within 4 standard deviations of the closed form.
+sums of every level within the FP32 evaluation tolerance of the oracle run on
+the same (23-bit) uniforms, decisions consistent with the kernel's own
+statistics and equal to the oracle's except within FP32's reach of a tie, and
+the value within 3 standard deviations of the closed form.
 """
 import math
 
@@ -16,8 +17,8 @@ from oracle import closed_forms as CF
 from oracle import zmc_oracle as O
 from paper_1902_07916_gb300.workloads import Workload, sin3d
 
-from parity import (check_decisions_consistent, compare_fp64, run_gpu, run_oracle,
-                    sums_tolerance)
+from parity import (check_decisions_consistent, compare_fp64, fp32_levels_against_oracle,
+                    run_gpu, run_oracle, sums_tolerance)
 
 pytestmark = pytest.mark.gpu
 
@@ -175,13 +176,13 @@ FP32_CASES = [
 def test_fp32_modes_within_stated_tolerance(zmc, w, _, prec):
     res, levels = run_gpu(zmc, w, prec)
     ref = run_oracle(w, fp32_uniforms=True)
-    # level-1 sums: FP32 points and integrand against FP64 on the same uniforms
-    g, r = levels[0], ref.levels[0]
-    err = np.abs(g["sums"] - r.sums)
-    assert np.all(err <= sums_tolerance(r.sums, w.n, 2e-5)), float(err.max())
+    # every level's sums: FP32 points and integrand against FP64 on the same
+    # uniforms; decisions consistent with the kernel's own spreads and, where
+    # the trees agree, the oracle's except within FP32's reach of a tie
+    fp32_levels_against_oracle(w, levels, ref)
     check_decisions_consistent(w, levels, res)
     exact = CF.integral(w.integrand, w.lo, w.hi, w.params)
-    assert abs(res.value - exact) <= 4 * res.std + 1e-6 * abs(exact), (res.value, exact, res.std)
+    assert abs(res.value - exact) <= 3 * res.std, (res.value, exact, res.std)
 
 
 @pytest.mark.parametrize("prec", ["fp32_fp64acc", "fp32_kahan"])
@@ -238,7 +239,7 @@ def test_fp32_sine_of_large_arguments(zmc, prec):
     assert np.all(err <= w.n * e_point), (float(err.max()), w.n * e_point)
     assert res.flagged_per_level == ref.flagged_per_level
     exact = CF.integral(w.integrand, w.lo, w.hi, w.params)
-    assert abs(res.value - exact) <= 4 * res.std + 1e-3 * abs(exact), (res.value, exact, res.std)
+    assert abs(res.value - exact) <= 3 * res.std, (res.value, exact, res.std)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_fp64acc"])
