@@ -10,8 +10,15 @@ level, 2^40 points per run).  The metric is points evaluated per second
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Beside the headline the line carries: the same workload in FP64 and in the
+FP32-Kahan mode; the 512-integral batch; the 8-D corner peak in the three
+precisions; time to a relative error of 1e-4 (9-D Gaussian); the paper's
+parameter sets (Sec. 3); the kernels' arithmetic error against the oracle on
+sampled level-1 tiles; and the oracle timed on the host cores.
+
 --impl reference times the FP64 CPU oracle (the from-scratch reference of
 the method) on the host cores, on a bounded sample of the same workload.
+--peaks measures the pipe rates that bound the sampling kernel.
 Under torchrun every rank integrates its own independent problem (seed +
 rank): weak scaling, no collective on the data path.
 """
@@ -52,8 +59,14 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     p.add_argument("--no-batch", action="store_true", help="skip the batched leg")
     p.add_argument("--no-tta", action="store_true", help="skip the time-to-accuracy leg")
+    p.add_argument("--no-legs", action="store_true",
+                   help="skip the FP32-Kahan, corner-peak and paper-parameter legs")
     p.add_argument("--paper", action="store_true",
                    help="run the paper's parameter sets (Sec. 3) instead of the benchmark")
+    p.add_argument("--peaks", action="store_true",
+                   help="measure the pipe rates that bound the sampling kernel (zmc_pipe_probe)")
+    p.add_argument("--peaks-iters", type=int, default=None,
+                   help="fixed iterations per probe kind (small profiling runs)")
     return p.parse_args()
 
 
@@ -366,9 +379,38 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_tta:
         tta = run_tta(zmc, stream)
 
+    kahan = corner = paper = None
+    traces = {}
+    if rank == 0 and not args.no_legs:
+        from paper_1902_07916_gb300 import workloads as wl
+        if prec != zmc.ZMC_FP32_KAHAN:
+            kahan = run_leg(zmc, w.with_(seed=seed), "fp32_kahan", stream)
+        # the 8-D corner peak (k=4, n=2^15, 16 trials, depth 5, m=1) in the
+        # three precisions: compensated FP32 against FP64 accumulation
+        cw = wl.corner8d()
+        corner = {"workload": "corner8d: Genz corner peak (1 + a.x)^-9 on [0,1]^8, a_i ~ "
+                              "U(0.5,5) from seed 0, k=4, n=2^15, trials=16, depth=5, m=1, "
+                              "default budget", "legs": [run_leg(zmc, cw, p, stream)
+                                                         for p in ("fp32_kahan", "fp32_fp64acc",
+                                                                   "fp64")]}
+        paper = paper_rows(zmc, stream)
+        if world == 1 and not args.no_cpu:
+            for p in dict.fromkeys([args.precision, "fp32_kahan", "fp64"]):
+                traces[("head", p)] = level1_sums(zmc, w.with_(seed=seed), p, stream)
+            for p in ("fp32_kahan", "fp32_fp64acc", "fp64"):
+                traces[("corner", p)] = level1_sums(zmc, cw, p, stream)
+
     cpu = None
+    mixed_error = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, target_s=12.0)
+        if traces:
+            # the kernels' arithmetic error against the oracle, per precision
+            ww = w.with_(seed=seed)
+            mixed_error = {"headline_workload": [error_vs_oracle(ww, p, traces[("head", p)])
+                                                 for (kind, p) in traces if kind == "head"],
+                           "corner8d": [error_vs_oracle(cw, p, traces[("corner", p)])
+                                        for (kind, p) in traces if kind == "corner"]}
 
     if rank != 0:
         return None
@@ -425,11 +467,122 @@ def run_ours(args, world, rank, local):
                 "d2h_bytes_per_step": d2h_bytes},
         "gpu_launches": kernels_per_run * args.steps,
         "fp64": fp64,
+        "fp32_kahan": kahan,
         "batched": batched,
+        "corner8d": corner,
         "time_to_accuracy": tta,
+        "paper": paper,
+        "mixed_error_vs_oracle": mixed_error,
         "cpu_baseline": cpu,
     }
     return line
+
+
+# ------------------------------------------------------- precision legs
+
+def run_leg(zmc, w, prec_name, stream, steps=2):
+    """One workload in one precision: a warm-up run (launch-shape tuning,
+    graph capture), then `steps` timed runs of the captured graph with CUDA
+    events on the launching stream, L2 flushed before each."""
+    import torch
+    prec = zmc.PRECISIONS[prec_name]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    with zmc.Integrator(w.dim, w.lo, w.hi, w.k, w.n, w.trials, w.depth, w.sigma_multiplier,
+                        w.seed, w.integrand, w.params, precision=prec) as it:
+        it.integrate(stream)
+        ms, r = [], None
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it.enqueue(stream)
+            e1.record(stream)
+            r = it.read_result(stream)
+            ms.append(e0.elapsed_time(e1))
+    try:
+        exact = exact_value(w)
+    except ValueError:
+        exact = None
+    return {"precision": prec_name, "value": round(r.samples * steps / (sum(ms) * 1e-3) / 1e9, 3),
+            "unit": UNIT, "steps": steps, "ms_per_step": round(sum(ms) / steps, 3),
+            "samples_per_step": r.samples, "result": r.value, "std": r.std, "exact": exact,
+            "result_minus_exact_over_std": (r.value - exact) / r.std
+            if exact is not None and r.std > 0 else None,
+            "levels_run": r.levels_run, "flagged_per_level": r.flagged_per_level,
+            "status": r.status}
+
+
+def level1_sums(zmc, w, prec_name, stream):
+    """Level-1 (S1, S2) per (cell, trial) as the sampling kernel produced them:
+    a traced depth-1 run (level 1's streams and work units do not depend on
+    the depth)."""
+    with zmc.Integrator(w.dim, w.lo, w.hi, w.k, w.n, w.trials, 1, w.sigma_multiplier, w.seed,
+                        w.integrand, w.params, precision=zmc.PRECISIONS[prec_name]) as it:
+        it.trace(True)
+        it.integrate(stream)
+        return it.trace_level(1)["sums"]
+
+
+ERROR_TILES = 64
+
+
+def error_vs_oracle(w, prec_name, sums):
+    """The kernel's arithmetic error on ERROR_TILES sampled level-1 cells (all
+    their trials): the FP64 oracle recomputes those tiles on the same points
+    (the FP32 stream for the FP32 modes).  S1 errors are given relative to
+    the tile's scale sqrt(n S2) + |S1| (S1 of an oscillating integrand cancels)
+    and per cell as the error of the cell's mean in units of its spread over
+    trials (arithmetic error against Monte Carlo noise)."""
+    import numpy as np
+    from oracle import zmc_oracle as O
+    C = sums.shape[0]
+    rng = np.random.default_rng(2024)
+    cells = np.sort(rng.choice(C, size=min(C, ERROR_TILES), replace=False))
+    ref = O.cell_sums(w.seed, 1, w.lo, w.hi, w.k, w.n, w.trials, w.integrand, w.params, cells,
+                      O.level1_cells(w.k, w.dim)[cells], fp32_uniforms=prec_name != "fp64")
+    got = sums[cells]
+    d1 = np.abs(got[..., 0] - ref[..., 0])
+    scale = np.sqrt(w.n * np.abs(ref[..., 1])) + np.abs(ref[..., 0])
+    volume = float(np.prod(O.level_widths(w.lo, w.hi, w.k, 1)))
+    _, mean_ref, spread_ref = O.cell_statistics(ref, volume, w.n)
+    _, mean_got, _ = O.cell_statistics(got, volume, w.n)
+    pos = spread_ref > 0
+    return {"precision": prec_name, "cells": int(cells.size), "tiles": int(cells.size * w.trials),
+            "points": int(cells.size * w.trials * w.n),
+            "stream": "FP64 stream" if prec_name == "fp64" else "FP32 stream",
+            "max_rel_s1_err": float("%.3g" % float(np.max(d1 / scale))),
+            "max_cell_mean_err_over_spread": float("%.3g" % float(
+                np.max(np.abs(mean_got - mean_ref)[pos] / spread_ref[pos]))) if pos.any() else None,
+            "test_tolerance_rel_s1": 1e-12 if prec_name == "fp64" else 2e-5}
+
+
+def paper_rows(zmc, stream, fp64_max_samples=int(4e9)):
+    """The paper's parameter sets (Sec. 3, Tab. 1-4) once each after a
+    warm-up, FP32-mixed for all and FP64 for those of at most
+    fp64_max_samples points; host wall clock around zmc_integrate."""
+    rows = []
+    for label, table, w in paper_runs():
+        exact = exact_value(w)
+        for prec in ("fp32_fp64acc", "fp64"):
+            if prec == "fp64" and w.k ** w.dim * w.n * w.trials > fp64_max_samples:
+                continue
+            with zmc.Integrator(w.dim, w.lo, w.hi, w.k, w.n, w.trials, w.depth,
+                                w.sigma_multiplier, w.seed, w.integrand, w.params,
+                                precision=zmc.PRECISIONS[prec]) as it:
+                it.integrate(stream)
+                t0 = time.perf_counter()
+                r = it.integrate(stream)
+                dt = time.perf_counter() - t0
+            rows.append({"run": label, "paper_table": table, "precision": prec,
+                         "cells_per_dim": w.k, "points_per_cell": w.n, "trials": w.trials,
+                         "depth": w.depth, "sigma_multiplier": w.sigma_multiplier,
+                         "result": r.value, "std": r.std, "closed_form": exact,
+                         "seconds": round(dt, 4), "samples": r.samples,
+                         "gsamples_per_s": round(r.samples / dt / 1e9, 2),
+                         "levels_run": r.levels_run, "flagged_per_level": r.flagged_per_level,
+                         "status": r.status})
+    return rows
 
 
 # ----------------------------------------------------------- batched leg
@@ -478,7 +631,7 @@ def run_batched(zmc, stream, prec, steps: int = 3):
 TTA_TARGET = 1e-4
 TTA_SEEDS = 5
 TTA_N = [1 << e for e in range(10, 23)]
-TTA_SWEEP_BUDGET_S = 120.0
+TTA_SWEEP_BUDGET_S = 90.0
 TTA_FP64_BUDGET_S = 75.0
 
 
@@ -495,7 +648,26 @@ def exact_value(w) -> float:
         for l, h in zip(w.lo, w.hi):
             z *= (complex(math.cos(h), math.sin(h)) - complex(math.cos(l), math.sin(l))) / 1j
         return z.imag
+    if w.integrand == "genz_corner":
+        return corner_peak_exact(w.lo, w.hi, w.params)
     raise ValueError("no closed form for " + w.integrand)
+
+
+def corner_peak_exact(lo, hi, a) -> float:
+    """int over the box of (1 + a.x)^-(d+1): integrating each dimension in
+    turn, 1 / (d! prod a_i) times the alternating sum over the box's vertices
+    v of (-1)^(number of upper coordinates of v) / (1 + a.v), in exact
+    rationals (the sum cancels badly in floating point)."""
+    from fractions import Fraction
+    import itertools
+    d = len(a)
+    fa = [Fraction(x) for x in a]
+    flo, fhi = [Fraction(x) for x in lo], [Fraction(x) for x in hi]
+    total = Fraction(0)
+    for upper in itertools.product((0, 1), repeat=d):
+        s = 1 + sum(ai * (h if u else l) for ai, l, h, u in zip(fa, flo, fhi, upper))
+        total += Fraction((-1) ** sum(upper)) / s
+    return float(total / (math.factorial(d) * math.prod(fa)))
 
 
 def median_first(firsts):
@@ -706,26 +878,104 @@ def run_paper(args):
     from paper_1902_07916_gb300 import zmc
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    rows = []
-    for label, table, w in paper_runs():
-        exact = exact_value(w)
-        for prec in ("fp64", "fp32_fp64acc"):
-            with zmc.Integrator(w.dim, w.lo, w.hi, w.k, w.n, w.trials, w.depth,
-                                w.sigma_multiplier, w.seed, w.integrand, w.params,
-                                precision=zmc.PRECISIONS[prec]) as it:
-                it.integrate(stream)
-                t0 = time.perf_counter()
-                r = it.integrate(stream)
-                dt = time.perf_counter() - t0
-            rows.append({"run": label, "paper_table": table, "precision": prec,
-                         "cells_per_dim": w.k, "points_per_cell": w.n, "trials": w.trials,
-                         "depth": w.depth, "sigma_multiplier": w.sigma_multiplier,
-                         "result": r.value, "std": r.std, "closed_form": exact,
-                         "seconds": round(dt, 4), "samples": r.samples,
-                         "gsamples_per_s": round(r.samples / dt / 1e9, 2),
-                         "levels_run": r.levels_run, "flagged_per_level": r.flagged_per_level,
-                         "status": r.status})
-    return {"paper_parameter_sets": rows, "gpu": torch.cuda.get_device_name(0)}
+    return {"paper_parameter_sets": paper_rows(zmc, stream, fp64_max_samples=1 << 62),
+            "gpu": torch.cuda.get_device_name(0)}
+
+
+# ------------------------------------------------------------ pipe rates
+
+# zmc_pipe_probe kinds: (name, kind id, what one chain step issues).  Every
+# thread runs 8 independent chains; one iteration is one step of each.
+PROBE_KINDS = [
+    ("imad_wide", 0, "one mad.wide.u32 (32x32->64-bit product)"),
+    ("imad", 1, "one mad.lo.u32"),
+    ("imad_hi", 2, "one mad.hi.u32"),
+    ("hilo_paired", 3, "high and low half of one product + a three-input XOR"),
+    ("hilo_split", 4, "the same, low half's multiplier from a kernel parameter"),
+    ("lop3", 5, "one three-input XOR"),
+    ("ffma", 6, "one FP32 fma"),
+    ("dfma", 7, "one FP64 fma"),
+    ("philox", 8, "one Philox4x32-10 block as the sampling kernel forms it"),
+    ("philox_split", 9, "one Philox4x32-10 block with split high/low products"),
+]
+PROBE_CHAINS = 8
+PROBE_THREADS = 256
+PROBE_CTAS_PER_SM = 4
+PROBE_TARGET_MS = 40.0
+
+
+def per_sm_rates(records, ops_per_cta):
+    """Rates from the CTAs' (clock64 start, end, ns start, end, smid) records:
+    per SM, the operations of the CTAs it ran over its own cycle span."""
+    by_sm = {}
+    for c0, c1, t0, t1, sm, _ in records:
+        by_sm.setdefault(sm, []).append((c0, c1, t0, t1))
+    rates, mhz, ctas = [], [], []
+    for recs in by_sm.values():
+        span = max(r[1] for r in recs) - min(r[0] for r in recs)
+        ns = max(r[3] for r in recs) - min(r[2] for r in recs)
+        rates.append(len(recs) * ops_per_cta / span)
+        mhz.append(1e3 * span / ns)
+        ctas.append(len(recs))
+    return rates, mhz, ctas
+
+
+def run_peaks(args):
+    """Every probe kind once at a calibrated length (about 40 ms), 4 CTAs of
+    256 threads per SM on average.  Rates are thread-level operations per SM
+    per clock: per SM, the work of the CTAs it ran over its own %clock64 span
+    (median over SMs); the SM clock the kernel saw is that span over the
+    %globaltimer span, and nvidia-smi's clocks are sampled alongside."""
+    import torch
+    from paper_1902_07916_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1902_07916_gb300 import zmc
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    blocks = sms * PROBE_CTAS_PER_SM
+    sink = torch.empty(blocks * PROBE_THREADS, dtype=torch.int32, device=dev)
+    clocks_buf = torch.empty(blocks * 6, dtype=torch.int64, device=dev)
+
+    def launch(kind, iters):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            zmc.zmc_pipe_probe(kind, iters, blocks, PROBE_THREADS, sink.data_ptr(),
+                               clocks_buf.data_ptr(), stream)
+            e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), clocks_buf.cpu().view(blocks, 6).tolist()
+
+    rows = {}
+    with ClockSampler(0) as clk:
+        for name, kind, what in PROBE_KINDS:
+            iters = args.peaks_iters
+            if iters is None:
+                base = 64 if name == "dfma" else 4096
+                launch(kind, base)                                  # warm-up
+                ms, _ = launch(kind, base)
+                iters = max(16, int(base * PROBE_TARGET_MS / max(ms, 1e-3)))
+            ms, recs = launch(kind, iters)
+            ops_cta = PROBE_THREADS * iters * PROBE_CHAINS
+            rates, mhz, ctas = per_sm_rates(recs, ops_cta)
+            rows[name] = {
+                "what": what, "iters": iters, "event_ms": round(ms, 4),
+                "per_sm_per_clk": round(statistics.median(rates), 3),
+                "per_sm_per_clk_min_max": [round(min(rates), 3), round(max(rates), 3)],
+                "warp_inst_per_sm_per_clk": round(statistics.median(rates) / 32, 4),
+                "sm_mhz_in_kernel": round(statistics.median(mhz), 1),
+                "ctas_per_sm_min_max": [min(ctas), max(ctas)], "sms_used": len(rates),
+                "event_rate_per_sm_per_clk_at_max_clock": round(
+                    blocks * ops_cta / (ms * 1e-3) / sms / (statistics.median(mhz) * 1e6), 3),
+            }
+    return {"pipe_rates": rows, "unit": "thread-level operations (or Philox blocks) per SM "
+            "per clock", "sms": sms, "ctas": blocks, "threads": PROBE_THREADS,
+            "chains_per_thread": PROBE_CHAINS, "gpu": torch.cuda.get_device_name(0),
+            "clocks": clk.summary()}
 
 
 def main():
@@ -733,6 +983,9 @@ def main():
     world, rank, local = dist_env()
     if args.paper:
         print(json.dumps(run_paper(args)), flush=True)
+        return
+    if args.peaks:
+        print(json.dumps(run_peaks(args)), flush=True)
         return
     if world > 1:
         import torch.distributed as dist

@@ -55,7 +55,9 @@ extern "C" {
 #define ZMC_ERR_NONFINITE 4    /* the integrand produced NaN or Inf         */
 #define ZMC_ERR_OOM 5          /* device memory could not be allocated      */
 #define ZMC_ERR_CUDA 6         /* a CUDA runtime call failed                */
-#define ZMC_ERR_TIMEOUT 7      /* a bounded device-side wait ran out        */
+#define ZMC_ERR_TIMEOUT 7      /* reserved for a bounded device-side wait;
+                                  no kernel of this library waits on another
+                                  CTA or kernel, so no call returns it      */
 #define ZMC_ERR_NOINTEGRAND 8  /* zmc_set_integrand was never called        */
 
 /* ------------------------------------------------------- precision modes */
@@ -161,8 +163,12 @@ ZMC_API int zmc_set_limits(zmc_handle h, int64_t max_cells_per_level,
  * threads = 0 (the default) lets the library's autotuner choose: on the
  * first run of a (precision, integrand, dimension) it times each candidate
  * shape once on a truncated level 1 of that problem and keeps the fastest
- * for the process (ZMC_TUNE=0 in the environment disables it).  Results do
- * not depend on the shape: the work units and their order of summation are
+ * for the process (ZMC_TUNE=0 in the environment disables it).  The timing
+ * runs go on the handle's own stream once the caller's stream has reached
+ * the call (an event, no device-wide synchronisation); when the caller's
+ * stream is being captured nothing is timed and the default shape (256
+ * threads, as many CTAs as fit) is used for that run.  Results do not
+ * depend on the shape: the work units and their order of summation are
  * fixed by the level's size, n and the precision.  Errors: ZMC_ERR_ARG.
  * zmc_launch_shape reports the shape of the last run (threads per CTA, CTAs).
  */
@@ -275,6 +281,44 @@ ZMC_API int zmc_run_info(zmc_handle h, int64_t* kernels, int64_t* h2d_bytes,
                          int64_t* d2h_bytes);
 
 /*
+ * zmc_pipe_probe -- measure one instruction kind's throughput on the current
+ * GPU (the paper has no counterpart: these are the roofline denominators of
+ * the sampling kernel, whose bound is integer work, for which no vendor peak
+ * is published).  Launches `blocks` CTAs of `threads` threads (a multiple of
+ * 32, at most 256); each thread runs 8 independent chains for `iters` steps:
+ *   ZMC_PROBE_IMAD_WIDE    one mad.wide.u32 (32x32 -> 64-bit) per step
+ *   ZMC_PROBE_IMAD         one mad.lo.u32
+ *   ZMC_PROBE_IMAD_HI      one mad.hi.u32
+ *   ZMC_PROBE_HILO_PAIRED  the high and low halves of one 32x32 product (as a
+ *                          Philox round needs them) and a three-input XOR
+ *   ZMC_PROBE_HILO_SPLIT   the same with the low half's multiplier held in a
+ *                          kernel parameter, so the two halves stay separate
+ *                          instructions
+ *   ZMC_PROBE_LOP3         one three-input XOR (lop3.b32)
+ *   ZMC_PROBE_FFMA         one FP32 fma;  ZMC_PROBE_DFMA  one FP64 fma
+ *   ZMC_PROBE_PHILOX       one Philox4x32-10 block as the sampling kernel
+ *                          forms it (17 wide products, 19 + 2 XORs, a 64-bit
+ *                          add)
+ *   ZMC_PROBE_PHILOX_SPLIT the same block with split high/low products
+ *   sink     device, blocks * threads uint32 out (keeps the work alive)
+ *   clocks   device, blocks * 6 int64 out: per CTA, %clock64 before and after
+ *            the loop, %globaltimer (ns) before and after, %smid, 0
+ * Asynchronous on `stream`.  Errors: ZMC_ERR_ARG, ZMC_ERR_CUDA.
+ */
+#define ZMC_PROBE_IMAD_WIDE 0
+#define ZMC_PROBE_IMAD 1
+#define ZMC_PROBE_IMAD_HI 2
+#define ZMC_PROBE_HILO_PAIRED 3
+#define ZMC_PROBE_HILO_SPLIT 4
+#define ZMC_PROBE_LOP3 5
+#define ZMC_PROBE_FFMA 6
+#define ZMC_PROBE_DFMA 7
+#define ZMC_PROBE_PHILOX 8
+#define ZMC_PROBE_PHILOX_SPLIT 9
+ZMC_API int zmc_pipe_probe(int kind, int64_t iters, int blocks, int threads, uint32_t* sink,
+                           int64_t* clocks, void* stream);
+
+/*
  * zmc_level_stats_noalloc -- one tree level's per-cell statistics and
  * threshold (the same arithmetic as the library's own selection step: trial
  * estimates I = volume * S1 / n, per-cell mean and sample spread, and
@@ -298,9 +342,14 @@ ZMC_API int zmc_run_info(zmc_handle h, int64_t* kernels, int64_t* h2d_bytes,
  * until the process exits, shared by all calls and keeping the last call's
  * contents (each call clears what must start at zero).  Calls that overlap
  * on the GPU (on different streams, or from different host threads) race on
- * it and must be serialised by the caller.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.
+ * it and must be serialised by the caller.  Every call looks up the array's
+ * device address on the current device (cudaGetSymbolAddress, which
+ * allocates nothing, so a reset of the device's context leaves no stale
+ * address behind); the first call on a device may load the library's device
+ * code there, so make it before any stream capture.  Non-finite sums are not
+ * reported (unlike zmc_integrate's ZMC_ERR_NONFINITE): a NaN or infinite S1
+ * makes that cell's mean and spread, and then mu, sigma and theta, NaN or
+ * infinite; callers that need the check test theta with isfinite.
  * Errors: ZMC_ERR_ARG (sizes beyond the bound, NULL pointers, bad values;
  * nothing is launched), ZMC_ERR_CUDA.
  */

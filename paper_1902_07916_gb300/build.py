@@ -20,7 +20,7 @@ LIB = os.path.join(BUILD, "libzmc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["eval_fp64.cu", "eval_fp32.cu", "eval_fp32k.cu", "batch_fp64.cu", "batch_fp32.cu",
-           "batch_fp32k.cu", "batch.cu", "select.cu", "api.cu", "jit.cu"]
+           "batch_fp32k.cu", "batch.cu", "select.cu", "api.cu", "jit.cu", "probe.cu"]
 # Device headers handed to NVRTC for expression integrands, under the names
 # their #include lines use.
 JIT_HEADERS = [

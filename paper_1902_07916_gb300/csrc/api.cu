@@ -3,6 +3,7 @@
 // tracing, and the single host <-> device crossing of a run.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -80,6 +81,24 @@ int cuda_fail(zmc_handle h, cudaError_t e, const char* what) {
     std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
     return fail(h, e == cudaErrorMemoryAllocation ? ZMC_ERR_OOM : ZMC_ERR_CUDA, msg);
 }
+
+// NVTX ranges (header-only NVTX3: without a profiler attached a push/pop is
+// a check of one pointer) around the API calls, the graph capture, the
+// launch-shape tuner and each level where the host sees levels (traced runs,
+// the batched form's per-level graphs); in a graph replay the levels run on
+// the device, timed by zmc_set_profiling's events instead.
+class Range {
+  public:
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    Range(const char* what, int level) {
+        char buf[48];
+        snprintf(buf, sizeof buf, "%s %d", what, level);
+        nvtxRangePushA(buf);
+    }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 bool fault_injected(const char* what) {
     const char* f = getenv("ZMC_FAULT");
@@ -362,7 +381,8 @@ float time_level1(zmc_ctx* h, Tuned c, int64_t cells, cudaEvent_t e0, cudaEvent_
     return ms;
 }
 
-Tuned tuned_shape(zmc_ctx* h) {
+Tuned tuned_shape(zmc_ctx* h, cudaStream_t s) {
+    Range range("zmc launch-shape tuner");
     if (h->launch_threads > 0) {
         const int occ = occupancy(eval_kernel(h), h->launch_threads);
         const int per_sm = h->launch_per_sm > 0 ? std::min(h->launch_per_sm, occ) : occ;
@@ -376,8 +396,26 @@ Tuned tuned_shape(zmc_ctx* h) {
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) return it->second;
     }
-    // the descriptor upload was enqueued on the caller's stream
-    if (cudaDeviceSynchronize() != cudaSuccess) return default_shape(h);
+    // Nothing may be timed while the caller's stream is being captured: the
+    // default shape then (not cached, so a later uncaptured run tunes).
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return default_shape(h);
+    }
+    // The timing runs go on the handle's own stream after the caller's stream
+    // has passed the descriptor upload (an event, not a device-wide sync, so
+    // other streams of the process keep running); each candidate waits only
+    // for its own end event.
+    cudaEvent_t ready = nullptr;
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ready, s) != cudaSuccess ||
+        cudaStreamWaitEvent(h->cap_stream, ready, 0) != cudaSuccess) {
+        if (ready) cudaEventDestroy(ready);
+        cudaGetLastError();
+        return default_shape(h);
+    }
+    cudaEventDestroy(ready);
     const int64_t K = ipow_sat(h->k, h->dim, INT64_MAX);
     const int64_t per_cell = h->n * (int64_t)h->T;
     const int64_t cells = std::max<int64_t>(1, std::min<int64_t>(K, (int64_t(1) << 29) / per_cell));
@@ -426,8 +464,8 @@ EvalShape eval_shape(zmc_ctx* h, int level, Tuned t) {
 }
 
 // Occupancy queries and tuning happen here, outside any stream capture.
-void plan_shapes(zmc_ctx* h) {
-    const Tuned t = tuned_shape(h);
+void plan_shapes(zmc_ctx* h, cudaStream_t s) {
+    const Tuned t = tuned_shape(h, s);
     for (int L = 1; L <= h->depth; ++L) h->shapes[L] = eval_shape(h, L, t);
 }
 
@@ -485,11 +523,12 @@ int ensure_events(zmc_ctx* h) {
     return ZMC_OK;
 }
 
-int ensure_graph(zmc_ctx* h) {
+int ensure_graph(zmc_ctx* h, cudaStream_t s) {
     if (!h->graph_stale && h->graph) return ZMC_OK;
+    Range range("zmc graph capture");
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
-    plan_shapes(h);
+    plan_shapes(h, s);
     if (int rc = ensure_events(h)) return rc;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
@@ -617,10 +656,11 @@ BatchCache g_batch;
 
 int run_traced(zmc_ctx* h, cudaStream_t s) {
     h->trace_levels.clear();
-    plan_shapes(h);
+    plan_shapes(h, s);
     if (int rc = ensure_events(h)) return rc;
     cudaError_t e = cudaSuccess;
     for (int L = 1; L <= h->depth; ++L) {
+        Range range("zmc level", L);
         e = enqueue_levels(h, s, L);
         if (e != cudaSuccess) return cuda_fail(h, e, "traced level launch");
         State st;
@@ -822,6 +862,7 @@ ZMC_API int zmc_trace_level(zmc_handle h, int level, int64_t* cells, int64_t* fl
 
 ZMC_API int zmc_enqueue(zmc_handle h, void* stream) {
     if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle");
+    Range range("zmc_enqueue");
     int rc = check_ready(h);
     if (rc) return rc;
     DeviceGuard g(h->device);
@@ -829,7 +870,7 @@ ZMC_API int zmc_enqueue(zmc_handle h, void* stream) {
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (h->desc_dirty && (rc = upload_desc(h, s))) return rc;
-    if ((rc = ensure_graph(h))) return rc;
+    if ((rc = ensure_graph(h, s))) return rc;
     cudaError_t e = cudaGraphLaunch(h->graph, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
     return ZMC_OK;
@@ -849,6 +890,7 @@ ZMC_API int zmc_read_result(zmc_handle h, void* stream, zmc_result* out) {
 
 ZMC_API int zmc_integrate(zmc_handle h, void* stream, zmc_result* out) {
     if (!h || !out) return fail(h, ZMC_ERR_ARG, "NULL argument");
+    Range range("zmc_integrate");
     int rc = check_ready(h);
     if (rc) return rc;
     DeviceGuard g(h->device);
@@ -859,7 +901,7 @@ ZMC_API int zmc_integrate(zmc_handle h, void* stream, zmc_result* out) {
     if (h->trace) {
         if ((rc = run_traced(h, s))) return rc;
     } else {
-        if ((rc = ensure_graph(h))) return rc;
+        if ((rc = ensure_graph(h, s))) return rc;
         cudaError_t e = cudaGraphLaunch(h->graph, s);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
     }
@@ -872,6 +914,7 @@ ZMC_API int zmc_integrate_batch(int count, const zmc_handle* hs, void* stream,
         return fail(nullptr, ZMC_ERR_ARG, "bad batch arguments");
     if (count == 0) return ZMC_OK;
     if (count > 65535) return fail(nullptr, ZMC_ERR_ARG, "at most 65535 integrals per batch");
+    Range range("zmc_integrate_batch");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
@@ -999,7 +1042,10 @@ ZMC_API int zmc_integrate_batch(int count, const zmc_handle* hs, void* stream,
     }
     // the integrals' parameters, every call; then every level; then results
     e = cudaMemcpyAsync(B.d_desc, B.h_desc, sizeof(Desc) * count, cudaMemcpyHostToDevice, s);
-    for (size_t L = 0; e == cudaSuccess && L < B.graphs.size(); ++L) e = cudaGraphLaunch(B.graphs[L], s);
+    for (size_t L = 0; e == cudaSuccess && L < B.graphs.size(); ++L) {
+        Range level("zmc batch level", (int)L + 1);
+        e = cudaGraphLaunch(B.graphs[L], s);
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(B.h_out, B.d_out, sizeof(zmc_result) * count, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1055,6 +1101,17 @@ ZMC_API int zmc_run_info(zmc_handle h, int64_t* kernels, int64_t* h2d_bytes, int
     if (kernels) *kernels = h->graph_kernels;
     if (h2d_bytes) *h2d_bytes = (int64_t)sizeof(Desc);
     if (d2h_bytes) *d2h_bytes = (int64_t)sizeof(zmc_result);
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_pipe_probe(int kind, int64_t iters, int blocks, int threads, uint32_t* sink,
+                           int64_t* clocks, void* stream) {
+    if (!pipe_probe_kind_valid(kind) || iters < 1 || blocks < 1 || threads < 32 ||
+        threads > 256 || threads % 32 != 0 || !sink || !clocks)
+        return fail(nullptr, ZMC_ERR_ARG, "bad probe arguments");
+    cudaError_t e = launch_pipe_probe(kind, iters, blocks, threads, sink, (long long*)clocks,
+                                      (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "probe launch");
     return ZMC_OK;
 }
 

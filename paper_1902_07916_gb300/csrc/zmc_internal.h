@@ -91,4 +91,9 @@ cudaError_t launch_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
                           uint32_t c3, int64_t count, uint32_t* out,
                           cudaStream_t s);
 
+// zmc_pipe_probe (probe.cu).
+bool pipe_probe_kind_valid(int kind);
+cudaError_t launch_pipe_probe(int kind, int64_t iters, int blocks, int threads, uint32_t* sink,
+                              long long* clocks, cudaStream_t s);
+
 }  // namespace zmc

@@ -113,6 +113,8 @@ def _load():
         "zmc_set_profiling": [H, ctypes.c_int],
         "zmc_profile": [H, P(ctypes.c_double), P(ctypes.c_int)],
         "zmc_run_info": [H, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)],
+        "zmc_pipe_probe": [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
         "zmc_level_stats_noalloc": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p],
@@ -282,6 +284,13 @@ def zmc_run_info(h):
     k, i, o = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(_lib.zmc_run_info(h, ctypes.byref(k), ctypes.byref(i), ctypes.byref(o)), h)
     return k.value, i.value, o.value
+
+
+def zmc_pipe_probe(kind, iters, blocks, threads, sink_ptr, clocks_ptr, stream=None):
+    """Device pointers: sink (blocks * threads uint32), clocks (blocks * 6 int64)."""
+    _check(_lib.zmc_pipe_probe(int(kind), int(iters), int(blocks), int(threads),
+                               ctypes.c_void_p(int(sink_ptr)), ctypes.c_void_p(int(clocks_ptr)),
+                               _stream_ptr(stream)))
 
 
 def zmc_level_stats_noalloc(sums_ptr, cells, trials, n, volume, sigma_multiplier,

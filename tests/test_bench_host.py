@@ -47,3 +47,17 @@ def test_fp32_flop_counts():
     assert bench.fp32_flops_per_sample("gauss_norm", 9) == 41
     # corner peak: r^(d+1) by binary powering, e = 9 = 0b1001: 4 squarings, 2 products
     assert bench.fp32_flops_per_sample("genz_corner", 8) == 2 * 8 + 4 + 2 + 3
+
+
+def test_corner_peak_closed_form():
+    # the benchmark's exact-rational corner peak against the oracle's, and in
+    # 1-D against the antiderivative: int_0^1 (1 + a x)^-2 dx = 1 / (1 + a)
+    w = workloads.corner8d()
+    assert math.isclose(bench.exact_value(w), CF.integral(w.integrand, w.lo, w.hi, w.params),
+                        rel_tol=1e-14)
+    assert math.isclose(bench.corner_peak_exact([0.0], [1.0], [3.0]), 0.25, rel_tol=1e-15)
+    # 2-D: (1/(2 a b)) [1 - 1/(1+a) - 1/(1+b) + 1/(1+a+b)]
+    a, b = 1.5, 4.0
+    want = (1 - 1 / (1 + a) - 1 / (1 + b) + 1 / (1 + a + b)) / (2 * a * b)
+    assert math.isclose(bench.corner_peak_exact([0.0, 0.0], [1.0, 1.0], [a, b]), want,
+                        rel_tol=1e-14)

@@ -4,9 +4,12 @@ integrands compiled at run time.
 Batch: every integral's result equals its single-integral result bit for
 bit (same sampling units, same selection grid), in all three precision
 modes, and FP64 batch results match the oracle.  Expressions: an expression
-for a registry integrand reproduces it to rounding, expressions with
-parameters and conditionals match the oracle-free closed forms, and a bad
-expression reports ZMC_ERR_COMPILE with the compiler's log.
+for a registry integrand reproduces it to rounding; expressions with
+parameters, conditionals, logic and special functions match the oracle's
+expression evaluator element by element (FP64: 1e-12 with identical
+decisions; FP32 modes: the FP32 tolerance on every level) and their closed
+forms within 3 standard deviations; a bad expression reports
+ZMC_ERR_COMPILE with the compiler's log.
 """
 import math
 
@@ -16,7 +19,8 @@ import pytest
 from oracle import closed_forms as CF
 from paper_1902_07916_gb300.workloads import Workload, genz_batch
 
-from parity import compare_fp64, run_gpu, run_oracle
+from parity import (check_decisions_consistent, compare_fp64,
+                    fp32_levels_against_oracle, run_gpu, run_oracle)
 
 pytestmark = pytest.mark.gpu
 
@@ -122,14 +126,59 @@ def test_expression_reproduces_registry_integrand(zmc):
     compare_fp64(w, res, levels, run_oracle(w))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32_fp64acc"])
-def test_expression_with_parameters_and_conditionals(zmc, precision):
-    # a step in x0 at p0 times a linear ramp in x1: closed form by hand
-    expr = "expr:(x[0] < p[0] ? p[1] : 0.0) * (1.0 + x[1])"
-    w = Workload("step", expr, 2, [0.0, 0.0], [1.0, 2.0], 4, 512, 6, 3, 1.0, 11, [0.37, 2.5])
-    res, _ = run_gpu(zmc, w, precision, trace=False)
-    exact = 2.5 * 0.37 * (2.0 + 2.0)      # int_0^0.37 2.5 dx0 * int_0^2 (1 + x1) dx1
-    assert abs(res.value - exact) <= 5 * res.std + 1e-12, (res.value, exact, res.std)
+EXPR_FP64 = [
+    # a step in x0 at p0 times a linear ramp in x1
+    Workload("step", "expr:(x[0] < p[0] ? p[1] : 0.0) * (1.0 + x[1])", 2, [0.0, 0.0],
+             [1.0, 2.0], 4, 512, 6, 3, 1.0, 11, [0.37, 2.5]),
+    # a special function, a conditional, parameters, and C's integer 1/2 (= 0)
+    Workload("erf_branch", "expr:erf(x[0] * p[2]) * (x[1] > p[0] ? exp(-x[1]) : p[1])"
+             " + fmax(x[2], p[2]) + 1/2", 3, [0.0] * 3, [1.0] * 3, 3, 301, 5, 3, 0.8, 6,
+             [0.5, 1.25, 0.3]),
+    # logic operators and nested conditionals
+    Workload("logic", "expr:(x[0] > 0.25 && x[1] < 0.75) || x[0] + x[1] > 1.5 ? "
+             "pow(x[0], 2.0) + 0.5 : (x[1] < 0.1 ? 3.0 : sqrt(x[1]))", 2, [0.0, 0.0],
+             [1.0, 1.0], 5, 97, 4, 3, 0.5, 9),
+]
+
+EXPR_FP32 = [
+    # conditionals continuous at their switch (FP32 rounding of a point near
+    # the switch then moves the value by rounding only)
+    Workload("erf_knee", "expr:erf(x[0]) * (x[1] > p[0] ? exp(-(x[1] - p[0])) : 1.0)", 2,
+             [0.0, 0.0], [1.0, 2.0], 3, 400, 5, 2, 1.0, 4, [0.5]),
+    Workload("hinge", "expr:fmax(x[0] - p[0], 0.0) * (x[1] < p[1] ? 1.0 + x[1] : "
+             "1.0 + p[1]) + cos(p[2] * x[2])", 3, [0.0] * 3, [1.0] * 3, 3, 256, 6, 2, 1.0, 8,
+             [0.4, 0.6, 3.0]),
+]
+
+
+@pytest.mark.parametrize("w", EXPR_FP64, ids=[w.name for w in EXPR_FP64])
+def test_expression_with_parameters_and_conditionals_fp64(zmc, w):
+    # element by element against the oracle's expression evaluator: sums at
+    # 1e-12, identical cell statistics, thresholds and flags, value at 1e-10
+    res, levels = run_gpu(zmc, w, "fp64")
+    compare_fp64(w, res, levels, run_oracle(w))
+
+
+@pytest.mark.parametrize("precision", ["fp32_fp64acc", "fp32_kahan"])
+@pytest.mark.parametrize("w", EXPR_FP32, ids=[w.name for w in EXPR_FP32])
+def test_expression_with_parameters_and_conditionals_fp32(zmc, w, precision):
+    res, levels = run_gpu(zmc, w, precision)
+    fp32_levels_against_oracle(w, levels, run_oracle(w, fp32_uniforms=True))
+    check_decisions_consistent(w, levels, res)
+
+
+def test_expression_closed_forms(zmc):
+    # the step: 2.5 * 0.37 * int_0^2 (1 + x1) dx1; the knee: int_0^1 erf *
+    # int_0^2 (x1 > 0.5 ? e^-(x1 - 0.5) : 1)
+    step, knee = EXPR_FP64[0], EXPR_FP32[0]
+    exact = {"step": 2.5 * 0.37 * 4.0,
+             "erf_knee": (math.erf(1.0) + (math.exp(-1.0) - 1.0) / math.sqrt(math.pi))
+             * (0.5 + 1.0 - math.exp(-1.5))}
+    for w in (step, knee):
+        for precision in ("fp64", "fp32_fp64acc"):
+            res, _ = run_gpu(zmc, w, precision, trace=False)
+            assert abs(res.value - exact[w.name]) <= 3 * res.std, (w.name, precision, res.value,
+                                                                   res.std)
 
 
 def test_expression_matches_closed_form_genz_gauss(zmc):
@@ -139,7 +188,7 @@ def test_expression_matches_closed_form_genz_gauss(zmc):
     w = Workload("gg", expr, 3, [0.0] * 3, [1.0] * 3, 3, 400, 6, 2, 1.0, 4, a + u)
     res, _ = run_gpu(zmc, w, "fp64", trace=False)
     exact = CF.genz_gauss([0.0] * 3, [1.0] * 3, a, u)
-    assert abs(res.value - exact) <= 5 * res.std, (res.value, exact, res.std)
+    assert abs(res.value - exact) <= 3 * res.std, (res.value, exact, res.std)
 
 
 def test_expression_compile_error_reports_log(zmc):
