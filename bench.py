@@ -67,6 +67,13 @@ def parse():
                    help="measure the pipe rates that bound the sampling kernel (zmc_pipe_probe)")
     p.add_argument("--peaks-iters", type=int, default=None,
                    help="fixed iterations per probe kind (small profiling runs)")
+    p.add_argument("--batch-compare", action="store_true",
+                   help="the 512-integral batch against the same integrals run one by one")
+    p.add_argument("--batch-count", type=int, default=512,
+                   help="integrals in --batch-compare (smaller: profiling cases)")
+    p.add_argument("--batch-level1", action="store_true",
+                   help="--batch-compare with level-1-only budgets and no single runs "
+                        "(a small case for ncu)")
     return p.parse_args()
 
 
@@ -436,6 +443,7 @@ def run_ours(args, world, rank, local):
             "samples_per_step": r.samples, "levels_run": r.levels_run,
             "cells_per_level": r.cells_per_level, "flagged_per_level": r.flagged_per_level,
             "status": r.status, "result": r.value, "std": r.std,
+            "work_plan": r.work_plan,
             "exact": exact,
             "result_minus_exact_over_std": (r.value - exact) / r.std
             if exact is not None and r.std > 0 else None,
@@ -978,6 +986,82 @@ def run_peaks(args):
             "clocks": clk.summary()}
 
 
+def run_batch_compare(args):
+    """The Genz batch through zmc_integrate_batch (best of three calls after a
+    warm-up) against the same integrals run one by one through zmc_integrate
+    (each after its own warm-up run), with points per second and the
+    fraction of the IMAD.WIDE roofline (17 d / 5 wide multiplies per point)
+    per dimension and per family."""
+    import collections
+    import torch
+    from paper_1902_07916_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1902_07916_gb300 import workloads, zmc
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = WIDE_MULS_PER_SM_CLK * sms * 2070e6
+    ws = workloads.genz_batch(args.batch_count, seed=0)
+    hs = []
+    try:
+        for w in ws:
+            h = zmc.zmc_create(w.dim, w.lo, w.hi, w.k, w.n, w.trials, w.depth,
+                               w.sigma_multiplier, w.seed)
+            hs.append(h)
+            zmc.zmc_set_integrand(h, w.integrand, w.params)
+            zmc.zmc_set_precision(h, args.precision)
+            budget = w.level1_samples() if args.batch_level1 else max(
+                BATCH_MAX_SAMPLES, w.level1_samples())
+            zmc.zmc_set_limits(h, 1 << 24, budget)
+        res = zmc.zmc_integrate_batch(hs, stream)
+        times = []
+        for _ in range(3 if not args.batch_level1 else 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = zmc.zmc_integrate_batch(hs, stream)
+            times.append(time.perf_counter() - t0)
+        tb = min(times)
+        out = {"integrals": len(ws), "precision": args.precision,
+               "batch_s": round(tb, 4), "batch_gsamples_s": round(
+                   sum(r.samples for r in res) / tb / 1e9, 2)}
+        if args.batch_level1:
+            return out
+        single = []
+        for w, h in zip(ws, hs):
+            zmc.zmc_integrate(h, stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = zmc.zmc_integrate(h, stream)
+            single.append((w, r, time.perf_counter() - t0))
+    finally:
+        for h in hs:
+            zmc.zmc_destroy(h)
+    ts = sum(s for _, _, s in single)
+    muls = lambda w, r: r.samples * philox_multiplies_per_sample(w.dim, False)
+    agg = collections.defaultdict(lambda: [0, 0.0, 0.0, 0])
+    for w, r, s in single:
+        for key in ("d=%d" % w.dim, w.integrand, "n=%d" % w.n):
+            a = agg[key]
+            a[0] += r.samples
+            a[1] += muls(w, r)
+            a[2] += s
+            a[3] += 1
+    all_muls = sum(muls(w, r) for w, r, _ in single)
+    out.update({
+        "singles_sum_s": round(ts, 4),
+        "singles_gsamples_s": round(sum(r.samples for _, r, _ in single) / ts / 1e9, 2),
+        "batch_wide_mult_frac": round(all_muls / tb / peak, 4),
+        "singles_wide_mult_frac": round(all_muls / ts / peak, 4),
+        "samples_weighted_dim": round(sum(r.samples * w.dim for w, r, _ in single)
+                                      / sum(r.samples for _, r, _ in single), 3),
+        "singles_by": {k: {"integrals": v[3], "seconds": round(v[2], 4),
+                           "gsamples_s": round(v[0] / v[2] / 1e9, 1),
+                           "wide_mult_frac": round(v[1] / v[2] / peak, 3)}
+                       for k, v in sorted(agg.items())},
+        "timing": "host wall clock around each call; peak = 32 IMAD.WIDE/clk/SM at 2070 MHz"})
+    return out
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -986,6 +1070,9 @@ def main():
         return
     if args.peaks:
         print(json.dumps(run_peaks(args)), flush=True)
+        return
+    if args.batch_compare:
+        print(json.dumps(run_batch_compare(args)), flush=True)
         return
     if world > 1:
         import torch.distributed as dist

@@ -80,6 +80,7 @@ extern "C" {
 
 #define ZMC_MAX_DIM 16
 #define ZMC_MAX_DEPTH 16
+#define ZMC_PLAN_FIELDS 5
 
 typedef struct zmc_ctx* zmc_handle;   /* opaque; owned by the library */
 
@@ -99,6 +100,10 @@ typedef struct zmc_result {
     /* min over the level's cells of |spread - theta| / theta: how close the
        closest selection decision was to a tie (+inf at the last level). */
     double min_margin_per_level[ZMC_MAX_DEPTH];
+    /* the work plan the run used (see zmc_set_work_plan): it fixes the order
+       in which every (cell, trial) sum was added up, so passing it back to
+       zmc_set_work_plan reproduces the result bit for bit */
+    int64_t work_plan[ZMC_PLAN_FIELDS];
 } zmc_result;
 
 /*
@@ -174,6 +179,39 @@ ZMC_API int zmc_set_limits(zmc_handle h, int64_t max_cells_per_level,
  */
 ZMC_API int zmc_set_launch(zmc_handle h, int threads, int ctas_per_sm);
 ZMC_API int zmc_launch_shape(zmc_handle h, int* threads, int* grid);
+
+/*
+ * zmc_set_work_plan -- how the sampling kernel cuts a level into work units
+ * (the paper leaves the GPU work decomposition open; its Numba kernels fix
+ * threads per block per experiment, Sec. 3.1-3.2).  Unlike the launch shape
+ * the plan decides the order in which each (cell, trial) sum is added up, so
+ * results depend on it at rounding level (FP64: about 1e-15 relative; FP32
+ * modes: about 1e-7), and every result records the plan it ran with
+ * (zmc_result::work_plan).  plan: host array of ZMC_PLAN_FIELDS int64:
+ *   [0] target_units          a level is cut into at least this many units
+ *                             when its tiles allow, 1 .. 2^18
+ *   [1] min_unit_groups       ... but no unit has fewer point groups (of 4
+ *                             points in FP64, 5 in the FP32 modes), >= 1:
+ *                             "samples per thread" is 1/32 of a unit
+ *   [2] lane_tile_groups      tiles of fewer groups always run one per lane
+ *   [3] lane_tile_max_groups  tiles of fewer groups run one per lane on ...
+ *   [4] lane_tile_min_tiles   ... levels of at least this many tiles, >= 1
+ * plan = NULL restores the default, {2^18, 1024, 64, 1024, 2^18}, or the
+ * tuned plan when ZMC_TUNE_PLAN is on.  Errors: ZMC_ERR_ARG.
+ *
+ * zmc_set_tuning -- what the autotuner may choose on a handle's first run:
+ * ZMC_TUNE_SHAPE (the default) the launch shape only, which never changes a
+ * result; ZMC_TUNE_PLAN also the work plan (lane_tile_min_tiles, then
+ * min_unit_groups), timed on the handle's own level 1 when that holds at
+ * most 2^31 points (larger levels keep the default), adopted only when at
+ * least 2% faster, cached per (kernel, dimension, n, level size) for the
+ * process and recorded in the results.  An explicit zmc_set_launch /
+ * zmc_set_work_plan wins over the tuner.  Errors: ZMC_ERR_ARG.
+ */
+#define ZMC_TUNE_SHAPE 1
+#define ZMC_TUNE_PLAN 2
+ZMC_API int zmc_set_work_plan(zmc_handle h, const int64_t* plan);
+ZMC_API int zmc_set_tuning(zmc_handle h, int flags);
 
 /*
  * zmc_integrate -- run the whole tree search on the current device and

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <tuple>
 #include <map>
 #include <mutex>
 #include <string>
@@ -59,6 +60,9 @@ struct zmc_ctx {
     bool desc_dirty = true;
     JitKernel jit{};                 // expression integrand, if any
     int launch_threads = 0, launch_per_sm = 0;  // 0: autotuned
+    int tuning = ZMC_TUNE_SHAPE;                // what the autotuner may choose
+    bool plan_set = false;                      // zmc_set_work_plan fixed the plan
+    WorkPlan plan = kDefaultPlan;               // the plan of the next / last run
     EvalShape shapes[ZMC_MAX_DEPTH + 1] = {};  // per level, set before capture
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -297,6 +301,7 @@ void build_desc(const zmc_ctx* h, Desc& D) {
     D.max_cells = h->max_cells;
     D.max_samples = h->max_samples;
     D.cap_cells = h->cap_cells;
+    D.plan = h->plan;
     for (int i = 0; i < h->dim; ++i) D.lo[i] = h->lo[i];
     for (int L = 1; L <= h->depth; ++L) {
         const double kL = (double)ipow_sat(h->k, L, INT64_MAX);   // exact below 2^53
@@ -389,7 +394,7 @@ Tuned tuned_shape(zmc_ctx* h, cudaStream_t s) {
         return Tuned{h->launch_threads, per_sm};
     }
     const char* env = getenv("ZMC_TUNE");
-    if (env && strcmp(env, "0") == 0) return default_shape(h);
+    if ((env && strcmp(env, "0") == 0) || !(h->tuning & ZMC_TUNE_SHAPE)) return default_shape(h);
     const std::pair<const void*, int> key(eval_kernel(h), h->dim);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -448,6 +453,97 @@ Tuned tuned_shape(zmc_ctx* h, cudaStream_t s) {
     return best;
 }
 
+// ---------------------------------------------------- work-plan tuner
+// With ZMC_TUNE_PLAN the tuner also chooses the work plan, which changes the
+// order of summation (so the choice is recorded in every result): level 1 of
+// the handle's own problem, whole, is timed under the tuned shape for
+// lane_tile_min_tiles in {2^15, 2^16, 2^17, 2^18, never}, then, with the best
+// of those, min_unit_groups in {256, 512, 1024, 2048, 4096}; a candidate
+// replaces the current one only when at least 2% faster.  Levels of more
+// than 2^31 points keep the default (there the plan's rules leave one unit
+// per tile and no lane tiles anyway).  Cached per (kernel, dimension, n,
+// level-1 tiles) for the process.
+struct PlanKey {
+    const void* kernel;
+    int d;
+    int64_t n, tiles;
+    bool operator<(const PlanKey& o) const {
+        return std::tie(kernel, d, n, tiles) < std::tie(o.kernel, o.d, o.n, o.tiles);
+    }
+};
+std::map<PlanKey, WorkPlan> g_tuned_plan;
+constexpr int64_t kPlanTuneMaxPoints = int64_t(1) << 31;
+
+float time_plan(zmc_ctx* h, Tuned shape, const WorkPlan& plan, cudaEvent_t e0, cudaEvent_t e1) {
+    const WorkPlan keep = h->plan;
+    h->plan = plan;
+    build_desc(h, *h->h_desc);
+    h->plan = keep;
+    cudaStream_t s = h->cap_stream;
+    if (cudaMemcpyAsync(h->buf.desc, h->h_desc, sizeof(Desc), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return -1.f;
+    return time_level1(h, shape, ipow_sat(h->k, h->dim, INT64_MAX), e0, e1);
+}
+
+WorkPlan tuned_plan(zmc_ctx* h, Tuned shape, cudaStream_t s) {
+    if (h->plan_set || !(h->tuning & ZMC_TUNE_PLAN) || h->integrand == kExpression)
+        return h->plan_set ? h->plan : kDefaultPlan;
+    const int64_t K = ipow_sat(h->k, h->dim, INT64_MAX);
+    if (K > kPlanTuneMaxPoints / (h->n * (int64_t)h->T)) return kDefaultPlan;
+    const PlanKey key{eval_kernel(h), h->dim, h->n, K * h->T};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned_plan.find(key);
+        if (it != g_tuned_plan.end()) return it->second;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return kDefaultPlan;
+    }
+    Range range("zmc work-plan tuner");
+    // The candidates' descriptors are staged in the handle's pinned buffer,
+    // which the caller's stream may still be copying from: wait (on the host)
+    // until that stream has passed this call's own upload.
+    cudaEvent_t ready = nullptr, e0 = nullptr, e1 = nullptr;
+    const bool ok = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess &&
+                    cudaEventRecord(ready, s) == cudaSuccess &&
+                    cudaEventSynchronize(ready) == cudaSuccess &&
+                    cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+    WorkPlan best = kDefaultPlan;
+    if (ok) {
+        time_plan(h, shape, best, e0, e1);   // warm-up
+        float best_ms = time_plan(h, shape, best, e0, e1);
+        auto consider = [&](WorkPlan c) {
+            const float ms = time_plan(h, shape, c, e0, e1);
+            if (ms > 0.f && best_ms > 0.f && ms < 0.98f * best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        };
+        for (int64_t t : {int64_t(1) << 15, int64_t(1) << 16, int64_t(1) << 17, INT64_MAX}) {
+            WorkPlan c = best;
+            c.lane_tile_min_tiles = t;
+            consider(c);
+        }
+        const WorkPlan base = best;
+        for (int64_t g : {256, 512, 2048, 4096}) {
+            WorkPlan c = base;
+            c.min_unit_groups = g;
+            consider(c);
+        }
+    }
+    for (cudaEvent_t e : {ready, e0, e1})
+        if (e) cudaEventDestroy(e);
+    cudaGetLastError();
+    if (ok) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tuned_plan[key] = best;
+    }
+    return best;
+}
+
 EvalShape eval_shape(zmc_ctx* h, int level, Tuned t) {
     EvalShape sh;
     sh.threads = t.threads;
@@ -456,17 +552,26 @@ EvalShape eval_shape(zmc_ctx* h, int level, Tuned t) {
         // no more CTAs than level 1 has units for their warps
         const int64_t tiles = ipow_sat(h->k, h->dim, INT64_MAX) * h->T;
         const int64_t units =
-            level_units(tiles, groups_of(h->n, h->mode), h->integrand != kExpression);
+            level_units(tiles, groups_of(h->n, h->mode), h->integrand != kExpression, h->plan);
         grid = std::min(grid, (units + t.threads / 32 - 1) / (t.threads / 32));
     }
     sh.grid = (int)std::max<int64_t>(grid, 1);
     return sh;
 }
 
-// Occupancy queries and tuning happen here, outside any stream capture.
-void plan_shapes(zmc_ctx* h, cudaStream_t s) {
+int upload_desc(zmc_ctx* h, cudaStream_t s);
+
+// Occupancy queries and tuning happen here, outside any stream capture.  If
+// the tuner chose another work plan, the run's descriptor is uploaded again
+// on the caller's stream (the tuner's own runs have finished by then).
+int plan_shapes(zmc_ctx* h, cudaStream_t s) {
     const Tuned t = tuned_shape(h, s);
+    const WorkPlan plan = tuned_plan(h, t, s);
+    const bool changed = memcmp(&plan, &h->plan, sizeof plan) != 0;
+    h->plan = plan;
     for (int L = 1; L <= h->depth; ++L) h->shapes[L] = eval_shape(h, L, t);
+    if (changed || (h->tuning & ZMC_TUNE_PLAN)) return upload_desc(h, s);
+    return ZMC_OK;
 }
 
 cudaError_t enqueue_eval(zmc_ctx* h, int level, const uint32_t* parents_prev, cudaStream_t s) {
@@ -528,7 +633,7 @@ int ensure_graph(zmc_ctx* h, cudaStream_t s) {
     Range range("zmc graph capture");
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
-    plan_shapes(h, s);
+    if (int rc = plan_shapes(h, s)) return rc;
     if (int rc = ensure_events(h)) return rc;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
@@ -564,6 +669,7 @@ int check_ready(zmc_ctx* h) {
 
 int finish_result(zmc_ctx* h, zmc_result* out) {
     *out = *h->h_result;
+    memcpy(out->work_plan, &h->plan, sizeof out->work_plan);
     if (out->status != ZMC_OK) {
         h->last_error = out->status == ZMC_ERR_BUDGET
                             ? "refinement stopped by the cell / sample budget"
@@ -656,7 +762,7 @@ BatchCache g_batch;
 
 int run_traced(zmc_ctx* h, cudaStream_t s) {
     h->trace_levels.clear();
-    plan_shapes(h, s);
+    if (int rc = plan_shapes(h, s)) return rc;
     if (int rc = ensure_events(h)) return rc;
     cudaError_t e = cudaSuccess;
     for (int L = 1; L <= h->depth; ++L) {
@@ -678,7 +784,7 @@ int run_traced(zmc_ctx* h, cudaStream_t s) {
             tl.parents_out.resize((size_t)tl.flagged * h->dim);
             const uint32_t* next = h->buf.parents[(L + 1) & 1];
             // the statistics kernel left each tile's total in its first unit slot
-            const int64_t chunks = unit_chunks(tl.cells * h->T, groups_of(h->n, h->mode));
+            const int64_t chunks = unit_chunks(tl.cells * h->T, groups_of(h->n, h->mode), h->plan);
             e = cudaMemcpy2D(tl.sums.data(), sizeof(double2), h->buf.sums,
                              sizeof(double2) * (size_t)chunks, sizeof(double2),
                              (size_t)tl.cells * h->T, cudaMemcpyDeviceToHost);
@@ -823,6 +929,39 @@ ZMC_API int zmc_set_launch(zmc_handle h, int threads, int ctas_per_sm) {
     if (ctas_per_sm < 0) return fail(h, ZMC_ERR_ARG, "ctas_per_sm must be >= 0");
     h->launch_threads = threads;
     h->launch_per_sm = ctas_per_sm;
+    h->graph_stale = true;
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_set_work_plan(zmc_handle h, const int64_t* plan) {
+    if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle");
+    if (!plan) {
+        h->plan_set = false;
+        h->plan = kDefaultPlan;
+    } else {
+        WorkPlan w;
+        memcpy(&w, plan, sizeof w);
+        if (w.target_units < 1 || w.target_units > kTargetUnits || w.min_unit_groups < 1 ||
+            w.lane_tile_groups < 0 || w.lane_tile_max_groups < 0 || w.lane_tile_min_tiles < 1)
+            return fail(h, ZMC_ERR_ARG,
+                        "work plan: need 1 <= target_units <= 2^18, min_unit_groups >= 1, "
+                        "lane_tile_groups >= 0, lane_tile_max_groups >= 0, "
+                        "lane_tile_min_tiles >= 1");
+        h->plan_set = true;
+        h->plan = w;
+    }
+    h->desc_dirty = true;
+    h->graph_stale = true;
+    return ZMC_OK;
+}
+
+ZMC_API int zmc_set_tuning(zmc_handle h, int flags) {
+    if (!h) return fail(nullptr, ZMC_ERR_ARG, "NULL handle");
+    if (flags & ~(ZMC_TUNE_SHAPE | ZMC_TUNE_PLAN))
+        return fail(h, ZMC_ERR_ARG, "tuning flags: ZMC_TUNE_SHAPE | ZMC_TUNE_PLAN");
+    h->tuning = flags;
+    if (!h->plan_set) h->plan = kDefaultPlan;
+    h->desc_dirty = true;
     h->graph_stale = true;
     return ZMC_OK;
 }
@@ -1053,6 +1192,7 @@ ZMC_API int zmc_integrate_batch(int count, const zmc_handle* hs, void* stream,
     int first = ZMC_OK;
     for (int i = 0; i < count; ++i) {
         outs[i] = B.h_out[i];
+        memcpy(outs[i].work_plan, &hs[i]->plan, sizeof outs[i].work_plan);
         // keep the handles' own descriptors in step for later single runs
         hs[i]->desc_dirty = true;
         if (outs[i].status != ZMC_OK && first == ZMC_OK) first = outs[i].status;

@@ -21,7 +21,7 @@ __global__ void zmc_batch_plan(const BatchEval* __restrict__ items, int count, i
         int64_t units = 0;
         if (C > 0) {
             const int64_t tiles = C * D.T;
-            units = level_units(tiles, groups_of(D.n, D.mode), true);
+            units = level_units(tiles, groups_of(D.n, D.mode), true, D.plan);
         }
         offsets[i + 1] = units;
     }

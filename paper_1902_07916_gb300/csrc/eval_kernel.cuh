@@ -1,9 +1,9 @@
 // Kernel (a): the fused sample-generate / evaluate / reduce kernel.
 //
-// Work is cut into units.  Usually a unit is a contiguous range of the point
-// groups of one (cell, trial) tile (unit_chunks() units per tile); for small
-// tiles on large levels (lane_tiles()) a unit is 32 consecutive whole tiles,
-// one per lane.  Every warp takes its first unit by its index and the rest
+// Work is cut into units by the descriptor's work plan.  Usually a unit is a
+// contiguous range of the point groups of one (cell, trial) tile
+// (unit_chunks() units per tile); for small tiles on large levels
+// (lane_tiles()) a unit is 32 consecutive whole tiles, one per lane.  Every warp takes its first unit by its index and the rest
 // from the level's atomic counter; the level's cell count is read from device
 // memory, so the host never needs it.  Per unit of one tile:
 //   1. lanes < d decode the cell's lattice coordinates from the slot index
@@ -20,8 +20,9 @@
 //      statistics kernel adds a tile's units in a fixed order.
 // A lane-tile unit does 1-3 per lane for its own tile and writes the tile's
 // sums without a warp reduction (lane_tile_unit).
-// No CTA-wide barrier is involved, and the summation order depends on n, d
-// and the level's size only -- not on the CTA size or grid chosen to run it.
+// No CTA-wide barrier is involved, and the summation order depends on n, d,
+// the level's size and the work plan (WorkPlan, in the descriptor) only --
+// not on the CTA size or grid chosen to run it.
 //
 // There is one kernel per dimension d in 1..16 and the dimension loop is
 // unrolled, so the Philox chains of successive dimensions interleave.
@@ -307,12 +308,12 @@ __device__ __forceinline__ void mask_tail(bool last, uint32_t tail, R (&f)[G], R
     }
 }
 
-// Decomposition of the level's work into units (see unit_chunks()).
+// Decomposition of the level's work into units (see WorkPlan).
 struct UnitPlan {
     int64_t units, chunks, tiles;
     uint32_t ngroups, tail;
     int T;
-    bool lane_tiles;   // a unit is 32 tiles, one per lane (see kLaneTileGroups)
+    bool lane_tiles;   // a unit is 32 tiles, one per lane (see WorkPlan)
 };
 
 template <int MODE>
@@ -323,16 +324,16 @@ __device__ __forceinline__ UnitPlan unit_plan(const Desc& D, int64_t C,
     p.ngroups = (uint32_t)groups_of(D.n, MODE);             // < 2^32: n * d < 2^34
     p.tail = (uint32_t)(D.n - (int64_t)kGroup<MODE> * (int64_t)(p.ngroups - 1));
     p.tiles = C * D.T;
-    p.lane_tiles = allow_lane_tiles && lane_tiles(p.tiles, p.ngroups);
-    p.chunks = unit_chunks(p.tiles, p.ngroups);          // 1 for lane tiles
-    p.units = level_units(p.tiles, p.ngroups, allow_lane_tiles);
+    p.lane_tiles = allow_lane_tiles && lane_tiles(p.tiles, p.ngroups, D.plan);
+    p.chunks = unit_chunks(p.tiles, p.ngroups, D.plan);  // 1 for lane tiles
+    p.units = level_units(p.tiles, p.ngroups, allow_lane_tiles, D.plan);
     return p;
 }
 
 // Distribution of a level's units over the warps of the sampling kernel:
 // a warp's first unit is its global warp index, every further one comes
-// from the level's counter in the tree state (one atomic per unit of >= 1024
-// point groups).  A unit's sums do not depend on which warp runs it, so the
+// from the level's counter in the tree state (one atomic per unit of at
+// least the plan's min_unit_groups point groups).  A unit's sums do not depend on which warp runs it, so the
 // results are the same under any order; the queue keeps every warp busy up
 // to the level's last unit, where a fixed stride leaves the warps that the
 // schedulers favoured idle at the end.

@@ -156,7 +156,7 @@ __device__ __forceinline__ void cell_stats_body(const Desc* __restrict__ desc, S
     // The sampling kernel left unit_chunks() partial sums per (cell, trial)
     // tile, contiguous per tile; add them in order and keep the total in the
     // tile's first slot.
-    const int64_t chunks = unit_chunks(C * T, groups_of(D.n, D.mode));
+    const int64_t chunks = unit_chunks(C * T, groups_of(D.n, D.mode), D.plan);
     bool finite = true;
     Moments acc{0.0, 0.0, 0.0};
     for (int64_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
@@ -256,7 +256,6 @@ __device__ __forceinline__ void flag_count_body(const Desc* __restrict__ desc, S
 
     // exclusive scan of the per-CTA counts (gridDim.x <= 32 * blockDim.x)
     __shared__ int64_t s_off[kSelGrid];
-    __shared__ double s_m[kSelGrid];
     if (threadIdx.x == 0) {
         int64_t run = 0;
         double m = INFINITY;
@@ -288,7 +287,6 @@ __device__ __forceinline__ void flag_count_body(const Desc* __restrict__ desc, S
         st->min_margin[level] = can_flag ? m : INFINITY;
         st->levels_run = level;
         st->ticket[1] = 0u;
-        s_m[0] = m;
     }
     __syncthreads();
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) part_offset[b] = s_off[b];

@@ -26,6 +26,30 @@ enum Integrand : int32_t {
     kExpression = 100,
 };
 
+// Work units of the sampling kernel, and therefore the order in which each
+// (cell, trial) sum is added up: a (cell, trial) tile is cut into `chunks`
+// units of about equal numbers of point groups so that a level has at least
+// target_units units when it can, but no unit has fewer than
+// min_unit_groups groups ("samples per thread": a lane takes one group in
+// 32 of its unit).  Lane tiles: a unit of 32 consecutive tiles, each lane one
+// whole tile, in place of one tile per warp (which leaves lanes idle on small
+// tiles and pays a per-tile set-up and FP64 warp reduction); taken for tiles
+// of fewer than lane_tile_groups point groups always, and for tiles of fewer
+// than lane_tile_max_groups groups when the level has at least
+// lane_tile_min_tiles tiles, enough units of 32 to keep every warp busy.
+// The registry kernels use lane tiles; expression kernels keep one tile per
+// warp.  Everything is a function of the plan, the level's tile count and n,
+// never of the GPU or the launch shape.  The field order is that of
+// zmc_result::work_plan.
+struct WorkPlan {
+    int64_t target_units;
+    int64_t min_unit_groups;
+    int64_t lane_tile_groups;
+    int64_t lane_tile_max_groups;
+    int64_t lane_tile_min_tiles;
+};
+static_assert(sizeof(WorkPlan) == ZMC_PLAN_FIELDS * 8, "WorkPlan is the result's work_plan");
+
 // Everything the kernels need to know about one integration, uploaded to
 // device memory before each run.  Plain old data, host-computed.
 struct Desc {
@@ -45,6 +69,7 @@ struct Desc {
     // rearranged on the host from the user's parameter list.
     double pa[ZMC_MAX_DIM], pb[ZMC_MAX_DIM];
     double c[4];
+    WorkPlan plan;                   // work decomposition of the sampling kernel
 };
 
 // Tree state of one run, written only by the kernels.  Index L = level.
@@ -63,13 +88,12 @@ struct State {
     unsigned long long queue[ZMC_MAX_DEPTH + 2];  // sampling units taken per level
 };
 
-// Work units of the sampling kernel.  A (cell, trial) tile is cut into
-// `chunks` units of about equal numbers of point groups so that a level
-// has at least kTargetUnits units when it can, but no unit has fewer than
-// kMinUnitGroups groups.  The count depends only on the level's tile count
-// and on n, never on the GPU, so neither do the results.
+
+
+// The default plan; target_units is also the most any plan may ask for (the
+// partial-sum buffer is sized for it).
 constexpr int64_t kTargetUnits = int64_t(1) << 18;
-constexpr int64_t kMinUnitGroups = 1024;
+constexpr WorkPlan kDefaultPlan = {kTargetUnits, 1024, 64, 1024, int64_t(1) << 18};
 
 // Points per Philox block in the mode's stream: four 32-bit words (FP64) or
 // five 23-bit fields (FP32 modes); a "group" is that many consecutive points.
@@ -89,40 +113,30 @@ inline int64_t groups_of(int64_t n, int mode) {
 #ifdef __CUDACC__
 __host__ __device__
 #endif
-inline int64_t unit_chunks(int64_t tiles, int64_t ngroups) {
+inline int64_t unit_chunks(int64_t tiles, int64_t ngroups, const WorkPlan& w) {
     if (tiles <= 0) return 1;
-    int64_t want = (kTargetUnits + tiles - 1) / tiles;
-    int64_t most = ngroups / kMinUnitGroups;
+    int64_t want = (w.target_units + tiles - 1) / tiles;
+    int64_t most = ngroups / w.min_unit_groups;
     if (most < 1) most = 1;
     return want < most ? (want < 1 ? 1 : want) : most;
 }
 
-// Lane tiles: a unit of 32 consecutive tiles, each lane one whole tile, in
-// place of one tile per warp (which leaves lanes idle on small tiles and pays
-// a per-tile set-up and FP64 warp reduction).  Taken for tiles of fewer than
-// kLaneTileGroups point groups always, and for tiles of fewer than
-// kMinUnitGroups groups (one unit per tile otherwise) when the level has at
-// least kLaneTileMinTiles tiles, enough units of 32 to keep every warp busy.
-// A function of the level's size and n only.  The registry kernels use it;
-// expression kernels keep one tile per warp.
-constexpr int64_t kLaneTileGroups = 64;
-constexpr int64_t kLaneTileMinTiles = int64_t(1) << 18;
-
 #ifdef __CUDACC__
 __host__ __device__
 #endif
-inline bool lane_tiles(int64_t tiles, int64_t ngroups) {
-    return ngroups < kLaneTileGroups ||
-           (ngroups < kMinUnitGroups && tiles >= kLaneTileMinTiles);
+inline bool lane_tiles(int64_t tiles, int64_t ngroups, const WorkPlan& w) {
+    return ngroups < w.lane_tile_groups ||
+           (ngroups < w.lane_tile_max_groups && tiles >= w.lane_tile_min_tiles);
 }
 
 // Work units of a level of `tiles` tiles of `ngroups` groups each.
 #ifdef __CUDACC__
 __host__ __device__
 #endif
-inline int64_t level_units(int64_t tiles, int64_t ngroups, bool allow_lane_tiles) {
-    if (allow_lane_tiles && lane_tiles(tiles, ngroups)) return (tiles + 31) / 32;
-    return tiles * unit_chunks(tiles, ngroups);
+inline int64_t level_units(int64_t tiles, int64_t ngroups, bool allow_lane_tiles,
+                           const WorkPlan& w) {
+    if (allow_lane_tiles && lane_tiles(tiles, ngroups, w)) return (tiles + 31) / 32;
+    return tiles * unit_chunks(tiles, ngroups, w);
 }
 
 }  // namespace zmc

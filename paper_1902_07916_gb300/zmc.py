@@ -37,6 +37,9 @@ PRECISIONS = {"fp64": ZMC_FP64, "fp32_fp64acc": ZMC_FP32_FP64ACC,
 
 ZMC_MAX_DIM = 16
 ZMC_MAX_DEPTH = 16
+ZMC_PLAN_FIELDS = 5
+ZMC_TUNE_SHAPE = 1
+ZMC_TUNE_PLAN = 2
 
 _D = ZMC_MAX_DEPTH
 
@@ -55,6 +58,7 @@ class zmc_result(ctypes.Structure):
         ("mu_per_level", ctypes.c_double * _D),
         ("sigma_per_level", ctypes.c_double * _D),
         ("min_margin_per_level", ctypes.c_double * _D),
+        ("work_plan", ctypes.c_int64 * ZMC_PLAN_FIELDS),
     ]
 
 
@@ -78,6 +82,7 @@ class Result:
     mu_per_level: list
     sigma_per_level: list
     min_margin_per_level: list
+    work_plan: list
 
 
 def _load():
@@ -110,6 +115,8 @@ def _load():
                          ctypes.c_void_p, ctypes.c_void_p],
         "zmc_set_launch": [H, ctypes.c_int, ctypes.c_int],
         "zmc_launch_shape": [H, P(ctypes.c_int), P(ctypes.c_int)],
+        "zmc_set_work_plan": [H, P(ctypes.c_int64)],
+        "zmc_set_tuning": [H, ctypes.c_int],
         "zmc_set_profiling": [H, ctypes.c_int],
         "zmc_profile": [H, P(ctypes.c_double), P(ctypes.c_int)],
         "zmc_run_info": [H, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)],
@@ -153,7 +160,8 @@ def _result(r: zmc_result) -> Result:
     return Result(r.value, r.std, r.cells_evaluated, r.samples, r.levels_run, r.status,
                   list(r.cells_per_level[:L]), list(r.flagged_per_level[:L]),
                   list(r.theta_per_level[:L]), list(r.mu_per_level[:L]),
-                  list(r.sigma_per_level[:L]), list(r.min_margin_per_level[:L]))
+                  list(r.sigma_per_level[:L]), list(r.min_margin_per_level[:L]),
+                  list(r.work_plan))
 
 
 def _doubles(values):
@@ -259,6 +267,19 @@ def zmc_uniforms(seed, level, slot, trial, dim, mode, first, count, out_ptr, str
 
 def zmc_set_launch(h, threads=0, ctas_per_sm=0):
     _check(_lib.zmc_set_launch(h, int(threads), int(ctas_per_sm)), h)
+
+
+def zmc_set_work_plan(h, plan=None):
+    """plan: five ints (target_units, min_unit_groups, lane_tile_groups,
+    lane_tile_max_groups, lane_tile_min_tiles), or None for the default."""
+    arr = None
+    if plan is not None:
+        arr = (ctypes.c_int64 * ZMC_PLAN_FIELDS)(*[int(v) for v in plan])
+    _check(_lib.zmc_set_work_plan(h, arr), h)
+
+
+def zmc_set_tuning(h, flags=ZMC_TUNE_SHAPE):
+    _check(_lib.zmc_set_tuning(h, int(flags)), h)
 
 
 def zmc_launch_shape(h):

@@ -39,8 +39,9 @@ def test_library_exports_every_declared_symbol(zmc):
 
 
 def test_result_struct_matches_header(zmc):
-    # 2 doubles, 2 int64, 2 int32, then 6 arrays of 16 eight-byte values
-    assert ctypes.sizeof(zmc.zmc_result) == 16 + 16 + 8 + 6 * 16 * 8
+    # 2 doubles, 2 int64, 2 int32, then 6 arrays of 16 eight-byte values and
+    # the five int64 of the work plan
+    assert ctypes.sizeof(zmc.zmc_result) == 16 + 16 + 8 + 6 * 16 * 8 + 5 * 8
 
 
 @pytest.mark.parametrize("kw,bad", [
@@ -125,3 +126,23 @@ def test_expression_compile_errors_without_a_device(zmc):
     with pytest.raises(zmc.ZmcError) as e:
         zmc.zmc_check_expression("", 2)
     assert e.value.code == zmc.ZMC_ERR_ARG
+
+
+def test_work_plan_and_tuning_validation_on_host(zmc):
+    h = zmc.zmc_create(3, [0.0] * 3, [1.0] * 3, 2, 16, 2, 1, 0.0, 0)
+    try:
+        for bad in ([0, 1024, 64, 1024, 1 << 18], [(1 << 18) + 1, 1024, 64, 1024, 1 << 18],
+                    [1 << 18, 0, 64, 1024, 1 << 18], [1 << 18, 1024, -1, 1024, 1 << 18],
+                    [1 << 18, 1024, 64, 1024, 0]):
+            with pytest.raises(zmc.ZmcError) as e:
+                zmc.zmc_set_work_plan(h, bad)
+            assert e.value.code == zmc.ZMC_ERR_ARG and "work plan" in zmc.zmc_last_error(h)
+        zmc.zmc_set_work_plan(h, [1 << 17, 512, 32, 512, 1 << 16])
+        zmc.zmc_set_work_plan(h, None)
+        with pytest.raises(zmc.ZmcError) as e:
+            zmc.zmc_set_tuning(h, 4)
+        assert e.value.code == zmc.ZMC_ERR_ARG
+        zmc.zmc_set_tuning(h, zmc.ZMC_TUNE_SHAPE | zmc.ZMC_TUNE_PLAN)
+        zmc.zmc_set_tuning(h, 0)
+    finally:
+        zmc.zmc_destroy(h)
