@@ -190,14 +190,14 @@ class ClockSampler:
 # --------------------------------------------------------- our arm
 
 def philox_multiplies_per_sample(d: int, fp64: bool) -> float:
-    """Algorithmic integer work per point: one Philox4x32-10 block per
-    dimension and group of points (four 32-bit words in the FP64 stream, five
-    23-bit fields in the FP32 stream).  A block is ten rounds of two
-    32x32->64-bit products; of those twenty, the two that depend only on
-    (trial, slot, level) are taken once per stream and round 1's product of
-    the block counter is an arithmetic progression (additions), which leaves
-    17 wide multiplies per block."""
-    return d / (4.0 if fp64 else 5.0) * 17
+    """Algorithmic integer work per point: per dimension and group of points
+    one Philox4x32-10 block in the FP64 stream (four 32-bit words, four
+    points) or a pair in the FP32 stream (eleven 23-bit fields, eleven
+    points).  A block is ten rounds of two 32x32->64-bit products; of those
+    twenty, the two that depend only on (trial, slot, level) are taken once
+    per stream and round 1's product of the block counter is an arithmetic
+    progression (additions), which leaves 17 wide multiplies per block."""
+    return d * (1.0 / 4.0 if fp64 else 2.0 / 11.0) * 17
 
 
 def fp32_flops_per_sample(integrand: str, d: int) -> int:
@@ -219,12 +219,13 @@ def fp32_flops_per_sample(integrand: str, d: int) -> int:
 
 def algorithmic_bytes_per_launch(cells_per_level, n, trials, fp64):
     """Bytes the sampling kernel must move per launch, averaged over the
-    step's levels: one (S1, S2) pair of doubles written per work unit (a
-    (cell, trial) tile is cut into `chunks` units so that a level has at
-    least 2^18 of them, each of at least 1024 point groups); its reads (the
+    step's levels: one (S1, S2) pair of doubles written per work unit (under
+    the default work plan a (cell, trial) tile is cut into `chunks` units so
+    that a level has at least 2^18 of them, each of at least 1024 point
+    groups of 4 points in FP64 or 11 in the FP32 modes); its reads (the
     parameters, 2.9 KB, and the parent list, 4 d bytes per flagged cell) are
     below 0.01% of that and left out."""
-    group = 4 if fp64 else 5
+    group = 4 if fp64 else 11
     ngroups = -(-n // group)
     total, launches = 0, 0
     for cells in cells_per_level:
@@ -248,7 +249,7 @@ TRAFFIC_CAPTURE = {
     "bytes_per_launch": (72704 + 0 + 11275776 + 171680768) / 2,
     "sources_sha256": "478a7e8ac92d7aea7367a779c70d0c2ef9ca931af83dc630af083a61a4f75f38",
 }
-KERNEL_SOURCES = ["eval_kernel.cuh", "zmc_device.cuh", "zmc_layout.h", "eval_fp32.cu"]
+KERNEL_SOURCES = ["eval_kernel.cuh", "zmc_device.cuh", "zmc_layout.h"]
 
 
 def kernel_sources_sha256() -> str:

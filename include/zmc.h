@@ -59,16 +59,18 @@ extern "C" {
                                   no kernel of this library waits on another
                                   CTA or kernel, so no call returns it      */
 #define ZMC_ERR_NOINTEGRAND 8  /* zmc_set_integrand was never called        */
+#define ZMC_ERR_CHECK 9        /* bounds-guarded build only: an index was out
+                                  of its buffer; the access was skipped     */
 
 /* ------------------------------------------------------- precision modes */
 #define ZMC_FP64 0             /* FP64 uniforms, points, integrand and sums */
 #define ZMC_FP32_FP64ACC 1     /* FP32 evaluation, FP32 partial sums over
-                                  80 points, FP64 per-thread and warp sums  */
+                                  88 points, FP64 per-thread and warp sums  */
 #define ZMC_FP32_KAHAN 2       /* FP32 evaluation, FP32 Kahan / two-sum
                                   accumulation up to the per-cell result     */
-/* The FP32 modes draw their points from the FP32 stream (five 23-bit
- * uniforms per Philox block, see zmc_uniforms), so they sample other points
- * than the FP64 mode does: their results differ from it by Monte Carlo
+/* The FP32 modes draw their points from the FP32 stream (eleven 23-bit
+ * uniforms per pair of Philox blocks, see zmc_uniforms), so they sample other
+ * points than the FP64 mode does: their results differ from it by Monte Carlo
  * noise as well as by rounding.  The Gaussian integrands ("gauss_norm",
  * "genz_gauss") are evaluated in the log2 domain in the FP32 modes (each
  * thread sums 2^(t - k) against its own reference exponent k, and the sums
@@ -292,8 +294,12 @@ ZMC_API int zmc_philox_words(uint64_t seed, uint32_t c0, uint32_t c1,
  *   mode ZMC_FP64: dimension i of points 4g..4g+3 are the four 32-bit words
  *     of the Philox4x32-10 block with counter (g*dim + i, trial, slot, level),
  *     u = (w + 1/2) 2^-32;
- *   mode ZMC_FP32_*: dimension i of points 5g..5g+4 are the five 23-bit
- *     fields of that block read as a 128-bit integer (bits 23f .. 23f+22),
+ *   mode ZMC_FP32_*: dimension i of points 11g..11g+10 come from the pair of
+ *     blocks with counters (2(g*dim + i), trial, slot, level) and
+ *     (2(g*dim + i) + 1, trial, slot, level), each read as a 128-bit
+ *     integer: points 0..4 of the group take the first block's 23-bit fields
+ *     (bits 23f .. 23f+22), points 5..9 the second block's, and point 10 the
+ *     first block's bits 115..127 below the second block's bits 115..124;
  *     u = (field + 1/2) 2^-23.
  * out: device pointer to count*dim doubles.  Asynchronous on `stream`.
  * Errors: ZMC_ERR_ARG, ZMC_ERR_CUDA.

@@ -15,17 +15,19 @@
  *
  * Random numbers are made at the point of use (Sec. 2.2); the paper names no
  * generator, so the stream is defined here as Philox4x32-10 (Salmon, Moraes,
- * Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11) with
- *     key     = (seed mod 2^32, seed div 2^32)
- *     counter = ((s div G) * d + i,  t,  q,  L)
- * for sample s in [0, n), dimension i in [0, d), trial t, work-list slot q and
- * level L (1-based).  One Philox block thus carries dimension i of G
- * consecutive samples:
- *   FP64 stream (G = 4): sample s reads 32-bit word (s mod 4), and
- *                        u = (w + 1/2) * 2^-32, exact in FP64;
- *   FP32 stream (G = 5): sample s reads 23-bit field (s mod 5) of the block
- *                        read as a 128-bit integer (bits 23 f .. 23 f + 22),
- *                        and u = (f + 1/2) * 2^-23, exact in FP32.
+ * Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11) with key
+ * (seed mod 2^32, seed div 2^32), for sample s in [0, n), dimension i in
+ * [0, d), trial t, work-list slot q and level L (1-based):
+ *   FP64 stream: sample s reads 32-bit word (s mod 4) of the block with
+ *                counter ((s div 4) d + i, t, q, L), u = (w + 1/2) 2^-32,
+ *                exact in FP64;
+ *   FP32 stream: with g = s div 11 and f = s mod 11, sample s reads, of the
+ *                pair of blocks with counters (2(g d + i), t, q, L) and
+ *                (2(g d + i) + 1, t, q, L) read as 128-bit integers A and B,
+ *                the 23-bit field f of A (bits 23 f .. 23 f + 22) for f < 5,
+ *                field f - 5 of B for 5 <= f < 10, and for f = 10 the value
+ *                (bits 115..127 of A) + 2^13 (bits 115..124 of B);
+ *                u = (field + 1/2) 2^-23, exact in FP32.
  * Both uniforms lie strictly inside (0, 1).
  * Sample:  x_i = lo_i + (c_i + u) * w_i, with c_i the cell's lattice
  *          coordinate at level L and w_i = (hi_i - lo_i) / k^L.
@@ -95,26 +97,50 @@ double zmc_oracle_field_uniform(uint32_t field) {
     return ((double)field + 0.5) * (1.0 / 8388608.0);
 }
 
+/* Bits [lo, lo + len) of a block read as the 128-bit integer above. */
+static uint32_t block_bits(const uint32_t w[4], int lo, int len) {
+    uint32_t out = 0;
+    for (int b = 0; b < len; ++b) {
+        const int bit = lo + b;
+        out |= ((w[bit / 32] >> (bit % 32)) & 1u) << b;
+    }
+    return out;
+}
+
+/* Field f (0..10) of a pair of blocks (a, b) in the FP32 stream. */
+uint32_t zmc_oracle_pair_field(const uint32_t a[4], const uint32_t b[4], int f) {
+    if (f < 5) return zmc_oracle_field23(a, f);
+    if (f < 10) return zmc_oracle_field23(b, f - 5);
+    return block_bits(a, 115, 13) | (block_bits(b, 115, 10) << 13);
+}
+
+/* The uniform of sample s, dimension i, of the (level, slot, trial) stream
+ * (the definitions in the header comment). */
+static double stream_uniform(const uint32_t key[2], int level, uint32_t slot, uint32_t trial,
+                             int d, int fp32, int64_t s, int i) {
+    uint32_t w[4];
+    if (!fp32) {
+        uint32_t ctr[4] = {(uint32_t)((s / 4) * d + i), trial, slot, (uint32_t)level};
+        zmc_oracle_philox4x32_10(ctr, key, w);
+        return zmc_oracle_uniform64(w[s % 4]);
+    }
+    uint32_t w2[4];
+    uint32_t ca[4] = {(uint32_t)(2 * ((s / 11) * d + i)), trial, slot, (uint32_t)level};
+    uint32_t cb[4] = {ca[0] + 1u, trial, slot, (uint32_t)level};
+    zmc_oracle_philox4x32_10(ca, key, w);
+    zmc_oracle_philox4x32_10(cb, key, w2);
+    return zmc_oracle_field_uniform(zmc_oracle_pair_field(w, w2, (int)(s % 11)));
+}
+
 /* Uniforms of the (level, slot, trial) stream for points [s0, s0 + count),
- * all d dimensions, point-major: out[(s - s0)*d + i].
- *   fp32 = 0: dimension i of points 4g..4g+3 is word (s mod 4) of the block
- *             with counter (g d + i, t, q, L), uniform (w + 1/2) / 2^32;
- *   fp32 = 1: dimension i of points 5g..5g+4 is field (s mod 5) of the
- *             block with counter (g d + i, t, q, L), uniform (f + 1/2) / 2^23. */
+ * all d dimensions, point-major: out[(s - s0)*d + i]; fp32 selects the FP32
+ * stream. */
 void zmc_oracle_stream_uniforms(uint64_t seed, int level, uint32_t slot, uint32_t trial,
                                 int d, int fp32, int64_t s0, int64_t count, double* out) {
     uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
-    const int G = fp32 ? 5 : 4;
-    for (int64_t s = s0; s < s0 + count; ++s) {
-        for (int i = 0; i < d; ++i) {
-            uint32_t ctr[4] = {(uint32_t)((s / G) * d + i), trial, slot, (uint32_t)level};
-            uint32_t w[4];
-            zmc_oracle_philox4x32_10(ctr, key, w);
-            out[(s - s0) * d + i] =
-                fp32 ? zmc_oracle_field_uniform(zmc_oracle_field23(w, (int)(s % G)))
-                     : zmc_oracle_uniform64(w[s % G]);
-        }
-    }
+    for (int64_t s = s0; s < s0 + count; ++s)
+        for (int i = 0; i < d; ++i)
+            out[(s - s0) * d + i] = stream_uniform(key, level, slot, trial, d, fp32, s, i);
 }
 
 /* Fill `out` with the words of the (level, slot, trial) stream for samples
@@ -224,24 +250,27 @@ static void one_cell_trial(const sums_job* J, int64_t cell, int trial) {
     uint32_t key[2] = {(uint32_t)(J->seed & 0xFFFFFFFFu),
                        (uint32_t)(J->seed >> 32)};
     double x[64];
-    uint32_t words[64][4];
+    uint32_t words[64][2][4];
     double S1 = 0.0, S2 = 0.0;
     const int64_t* c = J->coords + cell * d;
-    /* points per block: 4 words (FP64 stream) or 5 fields (FP32 stream) */
-    const int G = J->fp32_uniforms ? 5 : 4;
+    /* points per group: 4 words of one block (FP64 stream) or 11 fields of a
+       pair of blocks (FP32 stream) */
+    const int G = J->fp32_uniforms ? 11 : 4, B = J->fp32_uniforms ? 2 : 1;
     for (int64_t s = 0; s < J->n; ++s) {
         if (s % G == 0) {
-            /* the d Philox blocks that carry samples s .. s+G-1 */
-            for (int i = 0; i < d; ++i) {
-                uint32_t ctr[4] = {(uint32_t)((s / G) * d + i), (uint32_t)trial,
-                                   J->slots[cell], (uint32_t)J->level};
-                zmc_oracle_philox4x32_10(ctr, key, words[i]);
-            }
+            /* the d (pairs of) Philox blocks that carry samples s .. s+G-1 */
+            for (int i = 0; i < d; ++i)
+                for (int b = 0; b < B; ++b) {
+                    uint32_t ctr[4] = {(uint32_t)(B * ((s / G) * d + i) + b), (uint32_t)trial,
+                                       J->slots[cell], (uint32_t)J->level};
+                    zmc_oracle_philox4x32_10(ctr, key, words[i][b]);
+                }
         }
         for (int i = 0; i < d; ++i) {
             double u = J->fp32_uniforms
-                           ? zmc_oracle_field_uniform(zmc_oracle_field23(words[i], (int)(s % G)))
-                           : zmc_oracle_uniform64(words[i][s % G]);
+                           ? zmc_oracle_field_uniform(
+                                 zmc_oracle_pair_field(words[i][0], words[i][1], (int)(s % G)))
+                           : zmc_oracle_uniform64(words[i][0][s % G]);
             x[i] = J->lo[i] + ((double)c[i] + u) * J->width[i];
         }
         double f = zmc_oracle_integrand(J->integrand, d, x, J->params);
@@ -267,8 +296,9 @@ static void* sums_worker(void* arg) {
 
 /* For each requested cell of one level and each trial, the sums (S1, S2).
  * width[i] = (hi_i - lo_i) / k^level.  Returns 0, or -1 on bad arguments.
- * fp32_uniforms selects the FP32-evaluation stream (five 23-bit fields per
- * block): the points the FP32 modes sample; everything else stays FP64. */
+ * fp32_uniforms selects the FP32-evaluation stream (eleven 23-bit fields per
+ * pair of blocks): the points the FP32 modes sample; everything else stays
+ * FP64. */
 int zmc_oracle_cell_sums(uint64_t seed, int level, int d, const double* lo,
                          const double* width, int64_t n, int trials,
                          int integrand, const double* params, int64_t n_cells,

@@ -90,6 +90,9 @@ def _load():
         lib.zmc_oracle_field23.restype = ctypes.c_uint32
         lib.zmc_oracle_field_uniform.argtypes = [ctypes.c_uint32]
         lib.zmc_oracle_field_uniform.restype = ctypes.c_double
+        lib.zmc_oracle_pair_field.argtypes = [ctypes.POINTER(ctypes.c_uint32),
+                                              ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]
+        lib.zmc_oracle_pair_field.restype = ctypes.c_uint32
         lib.zmc_oracle_stream_uniforms.argtypes = [
             ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
             ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
@@ -161,6 +164,15 @@ def field23(block, f: int) -> int:
     return _load().zmc_oracle_field23(w, int(f))
 
 
+def pair_field(block_a, block_b, f: int) -> int:
+    """Field f (0..10) of a pair of blocks in the FP32 stream: fields 0..4 of
+    the first block, 5..9 of the second, and bits 115..127 of the first with
+    bits 115..124 of the second above them."""
+    a = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in block_a])
+    b = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in block_b])
+    return _load().zmc_oracle_pair_field(a, b, int(f))
+
+
 def field_uniform(field: int) -> float:
     """(f + 1/2) / 2^23: the FP32-stream uniform of a 23-bit field."""
     return _load().zmc_oracle_field_uniform(int(field))
@@ -170,7 +182,7 @@ def stream_uniforms(seed: int, level: int, slot: int, trial: int, d: int, fp32: 
                     s0: int, count: int) -> np.ndarray:
     """Uniforms of points [s0, s0 + count) of the (level, slot, trial) stream,
     shape (count, d): the FP64 stream (four 32-bit words per block) or the
-    FP32 stream (five 23-bit fields per block)."""
+    FP32 stream (eleven 23-bit fields per pair of blocks)."""
     lib = _load()
     out = np.zeros(count * d, dtype=np.float64)
     lib.zmc_oracle_stream_uniforms(seed, level, slot, trial, d, 1 if fp32 else 0, s0, count,

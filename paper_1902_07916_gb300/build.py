@@ -17,10 +17,20 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 GEN = os.path.join(BUILD, "gen")
 LIB = os.path.join(BUILD, "libzmc.so")
+# the bounds-guarded test build (ZMC_CHECKED): its own objects and library
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libzmc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["eval_fp64.cu", "eval_fp32.cu", "eval_fp32k.cu", "batch_fp64.cu", "batch_fp32.cu",
-           "batch_fp32k.cu", "batch.cu", "select.cu", "api.cu", "jit.cu", "probe.cu"]
+SOURCES = ["batch.cu", "select.cu", "api.cu", "jit.cu", "probe.cu"]
+# The sampling kernels, single-integral and batched, of each precision mode
+# (0: FP64, 1: FP32 + FP64 accumulation, 2: FP32 Kahan) in four parts of two
+# registry integrands each: one small generated translation unit per
+# (kind, mode, part), so that the heavy template instantiations compile in
+# parallel.
+KERNEL_PARTS = 4
+KERNEL_TUS = [(kind, mode, part) for kind in ("eval", "batch") for mode in (0, 1, 2)
+              for part in range(KERNEL_PARTS)]
 # Device headers handed to NVRTC for expression integrands, under the names
 # their #include lines use.
 JIT_HEADERS = [
@@ -31,7 +41,7 @@ JIT_HEADERS = [
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-         "--expt-relaxed-constexpr", "-I" + GEN, "-I" + INCLUDE]
+         "--expt-relaxed-constexpr", "-I" + GEN, "-I" + INCLUDE, "-I" + CSRC]
 
 
 def _nvcc() -> str:
@@ -62,45 +72,76 @@ def _gen_jit_sources() -> str:
     return path
 
 
+def _gen_kernel_tus() -> list:
+    """Write the per-(kind, mode, part) translation units into gen/ (only when
+    their text changes); returns their paths."""
+    os.makedirs(GEN, exist_ok=True)
+    paths = []
+    for kind, mode, part in KERNEL_TUS:
+        header = "eval_kernel.cuh" if kind == "eval" else "batch_kernel.cuh"
+        text = ("// generated by paper_1902_07916_gb300/build.py -- do not edit\n"
+                "#include \"%s\"\n#include \"zmc_internal.h\"\n\n"
+                "namespace zmc {\n"
+                "template <> const void* %s_kernel_part<%d, %d>(int fn, int d) {\n"
+                "    return %s_kernel_pair<%d, %d>(fn, d);\n}\n"
+                "}  // namespace zmc\n" % (header, kind, mode, part, kind, mode, part))
+        path = os.path.join(GEN, "%s_m%d_p%d.cu" % (kind, mode, part))
+        if not os.path.exists(path) or open(path).read() != text:
+            with open(path, "w") as fh:
+                fh.write(text)
+        paths.append(path)
+    return paths
+
+
 def _newest_input() -> float:
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     files += [os.path.join(INCLUDE, "zmc.h"), os.path.abspath(__file__)]
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile every translation unit and link libzmc.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          checked: bool = False) -> str:
+    """Compile every translation unit and link libzmc.so; returns its path.
+    checked=True builds the bounds-guarded test library instead
+    (ZMC_CHECKED, two registry integrands) into _build_checked/."""
+    build_dir = BUILD_CHECKED if checked else BUILD
+    lib = LIB_CHECKED if checked else LIB
+    os.makedirs(build_dir, exist_ok=True)
     _gen_jit_sources()
-    if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= _newest_input()):
-        return LIB
+    sources = [os.path.join(CSRC, f) for f in SOURCES] + _gen_kernel_tus()
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= _newest_input()):
+        return lib
     nvcc = _nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    if checked:
+        extra = extra + ["-DZMC_CHECKED"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(build_dir, os.path.splitext(os.path.basename(src))[0] + ".o")
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    # the longest units first, so the pool's tail is short
+    order = sorted(sources, key=lambda p: 0 if "_kernel_part" in p or "/gen/" in p else 1)
+    with cf.ThreadPoolExecutor(max_workers=max(2, os.cpu_count() or 2)) as ex:
+        results = list(ex.map(compile_one, order))
     if verbose or ptxas_info:
         for _, err in results:
             sys.stderr.write(err)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl", "-lpthread", "-lrt"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True,
-                ptxas_info="--ptxas-info" in sys.argv))
+                ptxas_info="--ptxas-info" in sys.argv, checked="--checked" in sys.argv))

@@ -18,13 +18,32 @@
 #include "jit.h"
 #include "zmc_internal.h"
 
-namespace zmc {
-const void* eval_kernel_fp64(int fn, int d);
-const void* eval_kernel_fp32_fp64acc(int fn, int d);
-const void* eval_kernel_fp32_kahan(int fn, int d);
-}  // namespace zmc
-
 using namespace zmc;
+
+namespace {
+// The sampling kernel of a registry integrand fn (0 .. kNumIntegrands - 1)
+// in mode MODE at dimension d, from the part that holds it.
+template <int MODE>
+const void* registry_kernel(int fn, int d, bool batched) {
+    switch (fn >> 1) {
+    case 0: return batched ? batch_kernel_part<MODE, 0>(fn, d) : eval_kernel_part<MODE, 0>(fn, d);
+    case 1: return batched ? batch_kernel_part<MODE, 1>(fn, d) : eval_kernel_part<MODE, 1>(fn, d);
+    case 2: return batched ? batch_kernel_part<MODE, 2>(fn, d) : eval_kernel_part<MODE, 2>(fn, d);
+    case 3: return batched ? batch_kernel_part<MODE, 3>(fn, d) : eval_kernel_part<MODE, 3>(fn, d);
+    default: return nullptr;
+    }
+}
+static_assert(kNumIntegrands == 2 * kKernelParts, "one part per pair of registry integrands");
+
+const void* registry_kernel(int mode, int fn, int d, bool batched) {
+    if (fn < 0 || fn >= kNumIntegrands) return nullptr;
+    switch (mode) {
+    case ZMC_FP64: return registry_kernel<ZMC_FP64>(fn, d, batched);
+    case ZMC_FP32_FP64ACC: return registry_kernel<ZMC_FP32_FP64ACC>(fn, d, batched);
+    default: return registry_kernel<ZMC_FP32_KAHAN>(fn, d, batched);
+    }
+}
+}  // namespace
 
 struct TraceLevel {
     int64_t cells = 0, flagged = 0;
@@ -301,6 +320,10 @@ void build_desc(const zmc_ctx* h, Desc& D) {
     D.max_cells = h->max_cells;
     D.max_samples = h->max_samples;
     D.cap_cells = h->cap_cells;
+    // ZMC_FAULT=capacity (a test of the bounds-guarded build): the kernels
+    // are told half of level 1's size as the capacity while the buffers keep
+    // their real size, so the guards fire on in-bounds memory
+    if (fault_injected("capacity")) D.cap_cells = std::max<int64_t>(1, D.K / 2);
     D.plan = h->plan;
     for (int i = 0; i < h->dim; ++i) D.lo[i] = h->lo[i];
     for (int L = 1; L <= h->depth; ++L) {
@@ -324,21 +347,11 @@ void build_desc(const zmc_ctx* h, Desc& D) {
     }
 }
 
-const void* batch_kernel(int mode, int fn, int d) {
-    switch (mode) {
-    case ZMC_FP64: return batch_kernel_fp64(fn, d);
-    case ZMC_FP32_FP64ACC: return batch_kernel_fp32_fp64acc(fn, d);
-    default: return batch_kernel_fp32_kahan(fn, d);
-    }
-}
+const void* batch_kernel(int mode, int fn, int d) { return registry_kernel(mode, fn, d, true); }
 
 const void* eval_kernel(const zmc_ctx* h) {
     if (h->integrand == kExpression) return h->jit.kernel;
-    switch (h->mode) {
-    case ZMC_FP64: return eval_kernel_fp64(h->integrand, h->dim);
-    case ZMC_FP32_FP64ACC: return eval_kernel_fp32_fp64acc(h->integrand, h->dim);
-    default: return eval_kernel_fp32_kahan(h->integrand, h->dim);
-    }
+    return registry_kernel(h->mode, h->integrand, h->dim, false);
 }
 
 // ------------------------------------------------------------ autotuner
@@ -550,9 +563,9 @@ EvalShape eval_shape(zmc_ctx* h, int level, Tuned t) {
     int64_t grid = (int64_t)h->num_sms * t.per_sm;
     if (level == 1) {
         // no more CTAs than level 1 has units for their warps
-        const int64_t tiles = ipow_sat(h->k, h->dim, INT64_MAX) * h->T;
-        const int64_t units =
-            level_units(tiles, groups_of(h->n, h->mode), h->integrand != kExpression, h->plan);
+        Desc D;
+        build_desc(h, D);
+        const int64_t units = level_plan(D, ipow_sat(h->k, h->dim, INT64_MAX)).units;
         grid = std::min(grid, (units + t.threads / 32 - 1) / (t.threads / 32));
     }
     sh.grid = (int)std::max<int64_t>(grid, 1);
@@ -664,12 +677,25 @@ int ensure_graph(zmc_ctx* h, cudaStream_t s) {
 
 int check_ready(zmc_ctx* h) {
     if (h->integrand < 0) return fail(h, ZMC_ERR_NOINTEGRAND, "zmc_set_integrand was not called");
+    if (!eval_kernel(h))
+        return fail(h, ZMC_ERR_ARG, "this build of the library has no sampling kernel for the "
+                                    "integrand (the bounds-guarded build carries sin_sum and "
+                                    "genz_corner only)");
     return ZMC_OK;
 }
 
 int finish_result(zmc_ctx* h, zmc_result* out) {
     *out = *h->h_result;
     memcpy(out->work_plan, &h->plan, sizeof out->work_plan);
+    if (out->status == ZMC_ERR_CHECK) {
+        State st;
+        uint32_t site = 0;
+        if (cudaMemcpy(&st, h->buf.state, sizeof st, cudaMemcpyDeviceToHost) == cudaSuccess)
+            site = st.check_site;
+        h->last_error = "bounds check failed (site " + std::to_string(site) +
+                        "): an index was outside its buffer; the access was skipped";
+        return out->status;
+    }
     if (out->status != ZMC_OK) {
         h->last_error = out->status == ZMC_ERR_BUDGET
                             ? "refinement stopped by the cell / sample budget"
@@ -784,7 +810,9 @@ int run_traced(zmc_ctx* h, cudaStream_t s) {
             tl.parents_out.resize((size_t)tl.flagged * h->dim);
             const uint32_t* next = h->buf.parents[(L + 1) & 1];
             // the statistics kernel left each tile's total in its first unit slot
-            const int64_t chunks = unit_chunks(tl.cells * h->T, groups_of(h->n, h->mode), h->plan);
+            Desc D;
+            build_desc(h, D);
+            const int64_t chunks = level_plan(D, tl.cells).chunks;
             e = cudaMemcpy2D(tl.sums.data(), sizeof(double2), h->buf.sums,
                              sizeof(double2) * (size_t)chunks, sizeof(double2),
                              (size_t)tl.cells * h->T, cudaMemcpyDeviceToHost);
@@ -1099,6 +1127,9 @@ ZMC_API int zmc_integrate_batch(int count, const zmc_handle* hs, void* stream,
         ev[i].keys = philox_keys(h->seed);
         ev[i].fn = h->integrand;
         kern[i] = batch_kernel(mode, ev[i].fn, h->dim);
+        if (!kern[i])
+            return fail(nullptr, ZMC_ERR_ARG, "this build of the library has no batched kernel "
+                                              "for an integrand of the batch");
         l1[i] = ipow_sat(h->k, h->dim, INT64_MAX);
         build_desc(h, B.h_desc[i]);
     }
@@ -1261,8 +1292,8 @@ ZMC_API int zmc_uniforms(uint64_t seed, int level, uint32_t slot, uint32_t trial
         (count > 0 && !out) ||
         (mode != ZMC_FP64 && mode != ZMC_FP32_FP64ACC && mode != ZMC_FP32_KAHAN))
         return fail(nullptr, ZMC_ERR_ARG, "bad arguments");
-    const int G = points_per_block(mode);
-    if (((first + count + G - 1) / G) * dim > 0xFFFFFFFFll)
+    const int G = points_per_group(mode), B = blocks_per_group(mode);
+    if (((first + count + G - 1) / G) * dim * B > 0xFFFFFFFFll)
         return fail(nullptr, ZMC_ERR_ARG, "points beyond the 2^32-block counter range");
     cudaError_t e = launch_uniforms(seed, level, slot, trial, dim, mode, first, count, out,
                                     (cudaStream_t)stream);

@@ -16,14 +16,8 @@ namespace zmc {
 __global__ void zmc_batch_plan(const BatchEval* __restrict__ items, int count, int level,
                                int64_t* __restrict__ offsets, unsigned long long* head) {
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
-        const Desc& D = *items[i].desc;
-        const int64_t C = items[i].st->cells[level];
-        int64_t units = 0;
-        if (C > 0) {
-            const int64_t tiles = C * D.T;
-            units = level_units(tiles, groups_of(D.n, D.mode), true, D.plan);
-        }
-        offsets[i + 1] = units;
+        const State* st = items[i].st;
+        offsets[i + 1] = st->cells[level] > 0 ? st->uplan[level].units : 0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -54,7 +54,7 @@ zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
         }
         const BatchEval& it = items[lo];
         const Desc& D = *it.desc;
-        const UnitPlan plan = unit_plan<MODE>(D, it.st->cells[level]);
+        const UnitPlan plan = it.st->uplan[level];
         const int64_t local = u - offsets[lo];
         if (lane < D.d) wp[lane] = (R)D.pb[lane];
         if (lane < 4) wcst[lane] = (R)D.c[lane];
@@ -64,7 +64,7 @@ zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
 #define ZMC_LANE_CASE(DD)                                                                     \
     case DD:                                                                                  \
         lane_tile_unit<MODE, FN, DD>(D, level, plan, local, it.parents[level & 1], keys, wc,  \
-                                     s_lane_beta[warp], wp, wcst, slot, it.sums);             \
+                                     s_lane_beta[warp], wp, wcst, slot, it.sums, it.st);      \
         break;
             if constexpr (HI) {
                 switch (D.d) {
@@ -84,7 +84,7 @@ zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
             continue;
         }
         const Unit un = unit_of(plan, local);
-        const R start = fold_setup<MODE, FN>(D, level, un.q, it.parents[level & 1], wc, wt);
+        const R start = fold_setup<MODE, FN>(D, level, un.q, it.parents[level & 1], wc, wt, it.st);
         const StreamConst sc = stream_const(keys, un.t, (uint32_t)un.q, (uint32_t)level);
         SumsFor<MODE, FN> acc(slot, value_scale<MODE, FN>(D));
 #define ZMC_BATCH_CASE(DD)                                                                    \
@@ -106,29 +106,30 @@ zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
             }
         }
 #undef ZMC_BATCH_CASE
-        acc.reduce_store(it.sums + local);
+        if (in_bounds(it.st, local, cap_partial_sums(D), kSiteUnitSum))
+            acc.reduce_store(it.sums + local);
         __syncwarp();   // the warp's shared slices are rewritten by its next unit
     }
 }
 
-// One mode's batched instantiations, indexed like eval_kernel_for().
-template <int MODE, bool HI>
-inline const void* batch_kernel_range(int fn) {
-    switch (fn) {
-    case kConstant: return (const void*)zmc_batch_eval<MODE, kConstant, HI>;
-    case kLinear: return (const void*)zmc_batch_eval<MODE, kLinear, HI>;
-    case kSinSum: return (const void*)zmc_batch_eval<MODE, kSinSum, HI>;
-    case kGaussNorm: return (const void*)zmc_batch_eval<MODE, kGaussNorm, HI>;
-    case kGenzOsc: return (const void*)zmc_batch_eval<MODE, kGenzOsc, HI>;
-    case kGenzProdPeak: return (const void*)zmc_batch_eval<MODE, kGenzProdPeak, HI>;
-    case kGenzGauss: return (const void*)zmc_batch_eval<MODE, kGenzGauss, HI>;
-    case kGenzCorner: return (const void*)zmc_batch_eval<MODE, kGenzCorner, HI>;
-    default: return nullptr;
-    }
+// One mode's batched instantiations, compiled in the same four parts as the
+// single-integral kernels (eval_kernel_pair): part p holds integrands 2p and
+// 2p + 1, each as a kernel for d in 1..8 and one for d in 9..16.
+template <int MODE, int FN>
+inline const void* batch_kernel_dims(int d) {
+    return d > 8 ? (const void*)zmc_batch_eval<MODE, FN, true>
+                 : (const void*)zmc_batch_eval<MODE, FN, false>;
 }
-template <int MODE>
-inline const void* batch_kernel_for(int fn, int d) {
-    return d > 8 ? batch_kernel_range<MODE, true>(fn) : batch_kernel_range<MODE, false>(fn);
+template <int MODE, int PART>
+inline const void* batch_kernel_pair(int fn, int d) {
+    constexpr int F0 = 2 * PART, F1 = 2 * PART + 1;
+    if constexpr (in_build<F0>()) {
+        if (fn == F0) return batch_kernel_dims<MODE, F0>(d);
+    }
+    if constexpr (in_build<F1>()) {
+        if (fn == F1) return batch_kernel_dims<MODE, F1>(d);
+    }
+    return nullptr;
 }
 
 }  // namespace zmc

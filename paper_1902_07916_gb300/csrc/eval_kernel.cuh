@@ -10,10 +10,11 @@
 //      (level 1: base-k digits; deeper: parent coordinates * k + child digit)
 //      and fold the cell's geometry into the integrand's per-dimension
 //      coefficients, in the warp's slice of shared memory;
-//   2. every lane takes groups of G consecutive samples (G = 4 in FP64, 5 in
-//      the FP32 modes); for each dimension one Philox4x32-10 block (counter
-//      (g*d + i, t, q, L)) gives that dimension's coordinate for all G
-//      samples -- four 32-bit words or five 23-bit fields (Sec. 2.2: random
+//   2. every lane takes groups of G consecutive samples (G = 4 in FP64, 11 in
+//      the FP32 modes); for each dimension one Philox4x32-10 block (FP64,
+//      counter (g*d + i, t, q, L): four 32-bit words) or a pair of blocks
+//      (FP32, counters 2(g*d + i) and 2(g*d + i) + 1: eleven 23-bit fields)
+//      gives that dimension's coordinate for all G samples (Sec. 2.2: random
 //      numbers are produced where they are used, nothing is stored);
 //   3. f and f^2 are summed per lane, then across the warp with shuffles, and
 //      lane 0 writes the unit's (S1, S2) to the partial-sum array.  The
@@ -32,7 +33,7 @@
 // each.
 //
 // MODE 0: FP64 throughout.  MODE 1: FP32 points and integrand, FP32 partial
-// sums over 16 groups (80 points) flushed into FP64 per-lane sums, FP64 warp
+// sums over 8 groups (88 points) flushed into FP64 per-lane sums, FP64 warp
 // reduction.  MODE 2: FP32 points and integrand with TwoSum-compensated
 // per-lane sums and a TwoSum warp reduction; the (sum, error) float pair is
 // widened to FP64 only for the stored result.  The Gaussian integrands run
@@ -48,12 +49,12 @@ constexpr int kEvalMaxWarps = kEvalMaxThreads / 32;
 // CTAs of kEvalMaxThreads per SM the register allocation must allow: caps
 // registers at 64 (FP32 modes) and 85 (FP64, whose values take two).
 template <int MODE>
-constexpr int eval_min_blocks() { return MODE == ZMC_FP64 ? 3 : 4; }
+constexpr int eval_min_blocks() { return 3; }
 // The dimension loop of a point group (group_values) is unrolled 8-way,
 // which covers d <= 8 completely; for d = 9..16 the FP32 modes unroll it
 // completely, since the remainder iteration of an 8-way unroll cost 2-4%.
 // FP64 keeps 8: its library exp and sin would spill under a full unroll.
-constexpr int kFlushGroups = 16;  // groups per FP32 partial sum (MODE 1)
+constexpr int kFlushGroups = 8;   // groups per FP32 partial sum (MODE 1): 88 points
 
 template <int MODE>
 struct ModeTraits {
@@ -66,14 +67,19 @@ struct ModeTraits<ZMC_FP64> {
     using R2 = double2;
 };
 
-// Points per block (and per group) of the mode's stream: 4 or 5.
+// Points per group of the mode's stream (4 or 11) and Philox blocks per
+// group and dimension (1 or 2).
 template <int MODE>
-constexpr int kGroup = MODE == ZMC_FP64 ? 4 : 5;
+constexpr int kGroup = MODE == ZMC_FP64 ? 4 : 11;
+template <int MODE>
+constexpr int kBlocks = MODE == ZMC_FP64 ? 1 : 2;
 
-// The G assembled 1.m values of one block: four 32-bit words (FP64 stream)
-// or five 23-bit fields (FP32 stream).
+// The G assembled 1.m values of one group and dimension: the four 32-bit
+// words of block w (FP64 stream), or the eleven 23-bit fields of the pair
+// (w, w2) (FP32 stream; w2 is unused in FP64).
 template <int MODE>
-__device__ __forceinline__ void block_points(uint4 w, typename ModeTraits<MODE>::R (&v)[kGroup<MODE>]) {
+__device__ __forceinline__ void block_points(uint4 w, uint4 w2,
+                                             typename ModeTraits<MODE>::R (&v)[kGroup<MODE>]) {
     if constexpr (MODE == ZMC_FP64) {
         v[0] = one_plus_word_f64(w.x);
         v[1] = one_plus_word_f64(w.y);
@@ -81,11 +87,23 @@ __device__ __forceinline__ void block_points(uint4 w, typename ModeTraits<MODE>:
         v[3] = one_plus_word_f64(w.w);
     } else {
         fields_1m(w, v[0], v[1], v[2], v[3], v[4]);
+        fields_1m(w2, v[5], v[6], v[7], v[8], v[9]);
+        v[10] = cross_1m(w, w2);
     }
 }
 
+// Sum and sum of squares of a group's eleven FP32 values, as a balanced tree.
+__device__ __forceinline__ void group_sums(const float (&f)[11], float& g1, float& g2) {
+    g1 = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) +
+         ((f[8] + f[9]) + f[10]);
+    const float q0 = fmaf(f[0], f[0], f[1] * f[1]), q1 = fmaf(f[2], f[2], f[3] * f[3]);
+    const float q2 = fmaf(f[4], f[4], f[5] * f[5]), q3 = fmaf(f[6], f[6], f[7] * f[7]);
+    const float q4 = fmaf(f[8], f[8], f[9] * f[9]);
+    g2 = ((q0 + q1) + (q2 + q3)) + fmaf(f[10], f[10], q4);
+}
+
 // Per-lane running sums of f and f^2 in the mode's arithmetic.  MODE 1 keeps
-// its FP64 sums in the lane's shared-memory slot (touched once per 64
+// its FP64 sums in the lane's shared-memory slot (touched once per 88
 // points), so they hold no registers in the sampling loop.
 template <int MODE>
 struct LaneSums {
@@ -97,7 +115,7 @@ struct LaneSums {
         if constexpr (MODE == ZMC_FP32_FP64ACC) *slot = make_double2(0.0, 0.0);
     }
 
-    // One group's values: four (FP64) or five (FP32) points.
+    // One group's values: four (FP64) or eleven (FP32) points.
     template <typename R>
     __device__ __forceinline__ void add(const R (&f)[kGroup<MODE>]) {
         if constexpr (MODE == ZMC_FP64) {
@@ -107,9 +125,8 @@ struct LaneSums {
                 S2d = fma(f[j], f[j], S2d);
             }
         } else {
-            const float g1 = ((f[0] + f[1]) + (f[2] + f[3])) + f[4];
-            const float g2 = fmaf(f[4], f[4], fmaf(f[0], f[0], f[1] * f[1]) +
-                                                  fmaf(f[2], f[2], f[3] * f[3]));
+            float g1, g2;
+            group_sums(f, g1, g2);
             if constexpr (MODE == ZMC_FP32_FP64ACC) {
                 s1 += g1;
                 s2 += g2;
@@ -210,9 +227,8 @@ struct LogLaneSums {
         float f[kGroup<MODE>];
 #pragma unroll
         for (int j = 0; j < kGroup<MODE>; ++j) f[j] = exp2f(t[j] - k);
-        const float g1 = ((f[0] + f[1]) + (f[2] + f[3])) + f[4];
-        const float g2 = fmaf(f[4], f[4], fmaf(f[0], f[0], f[1] * f[1]) +
-                                              fmaf(f[2], f[2], f[3] * f[3]));
+        float g1, g2;
+        group_sums(f, g1, g2);
         if constexpr (MODE == ZMC_FP32_FP64ACC) {
             s1 += g1;
             s2 += g2;
@@ -308,28 +324,6 @@ __device__ __forceinline__ void mask_tail(bool last, uint32_t tail, R (&f)[G], R
     }
 }
 
-// Decomposition of the level's work into units (see WorkPlan).
-struct UnitPlan {
-    int64_t units, chunks, tiles;
-    uint32_t ngroups, tail;
-    int T;
-    bool lane_tiles;   // a unit is 32 tiles, one per lane (see WorkPlan)
-};
-
-template <int MODE>
-__device__ __forceinline__ UnitPlan unit_plan(const Desc& D, int64_t C,
-                                              bool allow_lane_tiles = true) {
-    UnitPlan p;
-    p.T = D.T;
-    p.ngroups = (uint32_t)groups_of(D.n, MODE);             // < 2^32: n * d < 2^34
-    p.tail = (uint32_t)(D.n - (int64_t)kGroup<MODE> * (int64_t)(p.ngroups - 1));
-    p.tiles = C * D.T;
-    p.lane_tiles = allow_lane_tiles && lane_tiles(p.tiles, p.ngroups, D.plan);
-    p.chunks = unit_chunks(p.tiles, p.ngroups, D.plan);  // 1 for lane tiles
-    p.units = level_units(p.tiles, p.ngroups, allow_lane_tiles, D.plan);
-    return p;
-}
-
 // Distribution of a level's units over the warps of the sampling kernel:
 // a warp's first unit is its global warp index, every further one comes
 // from the level's counter in the tree state (one atomic per unit of at
@@ -374,9 +368,9 @@ __device__ __forceinline__ Unit unit_of(const UnitPlan& p, int64_t u) {
 // the point is x_i = w_L * 1.m + b_i = lo_i + (c_i + u) w_L.
 template <int MODE>
 __device__ __forceinline__ double cell_shift(const Desc& D, int level, int64_t q, int i,
-                                             const uint32_t* parents, double w) {
+                                             const uint32_t* parents, double w, const State* st) {
     const double s = (MODE == ZMC_FP64) ? 1.0 - 0x1p-33 : 1.0 - 0x1p-24;
-    const int64_t c = cell_coord(D, level, q, i, parents);
+    const int64_t c = cell_coord(D, level, q, i, parents, st);
     return D.lo[i] + (double)c * w - s * w;
 }
 
@@ -387,13 +381,13 @@ __device__ __forceinline__ double cell_shift(const Desc& D, int level, int64_t q
 template <int MODE, int FN>
 __device__ __forceinline__ typename ModeTraits<MODE>::R fold_setup(
     const Desc& D, int level, int64_t q, const uint32_t* parents,
-    typename ModeTraits<MODE>::R2* w_coef, double* w_term) {
+    typename ModeTraits<MODE>::R2* w_coef, double* w_term, const State* st) {
     using R = typename ModeTraits<MODE>::R;
     using F = Fn<FN, R>;
     const int lane = threadIdx.x & 31;
     if (lane < D.d) {
         const double w = D.width[level][lane];
-        const double b = cell_shift<MODE>(D, level, q, lane, parents, w);
+        const double b = cell_shift<MODE>(D, level, q, lane, parents, w, st);
         const Prep p = F::prep(w, b, D.pa[lane], D.pb[lane]);
         w_coef[lane].x = (R)p.alpha;
         w_coef[lane].y = (R)p.beta;
@@ -426,9 +420,9 @@ struct LaneCoef {
 };
 
 // The values of one point group (G points) of a registry integrand: the
-// Philox block of every dimension (round 1's product A * c0 given as P, the
-// 64-bit product for dimension 0), each folded into the G running sums, then
-// the finishing function.
+// Philox block (FP64) or pair of blocks (FP32) of every dimension (round 1's
+// product A * c0 given as P, the 64-bit product for the group's first block),
+// each folded into the G running sums, then the finishing function.
 template <int MODE, int FN, int DIM, class Coef>
 __device__ __forceinline__ void group_values(
     const PhiloxKeys& keys, const StreamConst& sc, const Coef& coef,
@@ -445,10 +439,15 @@ __device__ __forceinline__ void group_values(
     auto dimension = [&](int i) {
         const uint4 w = philox_from_product(keys, sc, (uint32_t)(P >> 32), (uint32_t)P);
         P += kPhiloxMulA;
+        uint4 w2 = w;
+        if constexpr (MODE != ZMC_FP64) {
+            w2 = philox_from_product(keys, sc, (uint32_t)(P >> 32), (uint32_t)P);
+            P += kPhiloxMulA;
+        }
         const R2 ab = coef(i);
         const R pb = s_pb[i];
         R v[G];
-        block_points<MODE>(w, v);
+        block_points<MODE>(w, w2, v);
 #pragma unroll
         for (int p = 0; p < G; ++p) a[p] = F::fold(a[p], v[p], ab.x, ab.y, pb);
     };
@@ -470,8 +469,9 @@ __device__ __forceinline__ void group_values(
 
 // The sample loop of one unit for a registry integrand, dimension DIM (a
 // compile-time constant, or 0 to take the dimension from dim_rt).
-// Round 1's product A * c0 is carried as a 64-bit running sum: c0 = g*d+i
-// grows by one per dimension and by 32*d per group of this lane.  Only the
+// Round 1's product A * c0 is carried as a 64-bit running sum: c0 =
+// B*(g*d + i) + b for the b-th of the B blocks of dimension i (B = 1 in FP64,
+// 2 in FP32) grows by one per block and by 32*B*d per group of this lane.  Only the
 // tile's last group can hold points past n; it is left out of the main loop
 // and run, masked, by the one lane it falls to in the unit that holds it.
 template <int MODE, int FN, int DIM>
@@ -483,9 +483,10 @@ __device__ __forceinline__ void sample_unit_fold(
     using R = typename ModeTraits<MODE>::R;
     using R2 = typename ModeTraits<MODE>::R2;
     const int nd = DIM > 0 ? DIM : dim_rt;
-    const uint64_t step = (uint64_t)kPhiloxMulA * (uint64_t)(32 * nd);
+    constexpr uint32_t B = kBlocks<MODE>;
+    const uint64_t step = (uint64_t)kPhiloxMulA * (uint64_t)(32 * B * nd);
     uint32_t g = g0 + (threadIdx.x & 31);
-    uint64_t Pg = (uint64_t)kPhiloxMulA * (uint64_t)(g * nd);
+    uint64_t Pg = (uint64_t)kPhiloxMulA * (uint64_t)(g * B * nd);
     constexpr int G = kGroup<MODE>;
     const uint32_t full_end = g1 <= last_group ? g1 : last_group;
     while (g < full_end) {
@@ -517,7 +518,7 @@ __device__ __forceinline__ void lane_tile_unit(
     const PhiloxKeys& keys, typename ModeTraits<MODE>::R2* w_coef,
     typename ModeTraits<MODE>::R* lane_beta,
     const typename ModeTraits<MODE>::R* s_pb, const typename ModeTraits<MODE>::R* s_c,
-    double2* slot, double2* partial) {
+    double2* slot, double2* partial, const State* st) {
     using R = typename ModeTraits<MODE>::R;
     using R2 = typename ModeTraits<MODE>::R2;
     using F = Fn<FN, R>;
@@ -530,7 +531,7 @@ __device__ __forceinline__ void lane_tile_unit(
     double a0 = (double)F::init();
     for (int i = 0; i < DIM; ++i) {
         const double w = D.width[level][i];
-        const double b = active ? cell_shift<MODE>(D, level, q, i, parents, w) : 0.0;
+        const double b = active ? cell_shift<MODE>(D, level, q, i, parents, w, st) : 0.0;
         const Prep p = F::prep(w, b, D.pa[i], D.pb[i]);
         if (lane == i) w_coef[i].x = (R)p.alpha;
         lane_beta[i * 32 + lane] = (R)p.beta;
@@ -542,7 +543,7 @@ __device__ __forceinline__ void lane_tile_unit(
     const LaneCoef<R, R2> coef{w_coef, lane_beta + lane};
     const StreamConst sc = stream_const(keys, t, (uint32_t)q, (uint32_t)level);
     SumsFor<MODE, FN> acc(slot, value_scale<MODE, FN>(D));
-    const uint64_t step = (uint64_t)kPhiloxMulA * (uint64_t)DIM;
+    const uint64_t step = (uint64_t)kPhiloxMulA * (uint64_t)(DIM * kBlocks<MODE>);
     const uint32_t last = plan.ngroups - 1;
     uint64_t Pg = 0;
     uint32_t g = 0;
@@ -559,7 +560,7 @@ __device__ __forceinline__ void lane_tile_unit(
     mask_tail(true, plan.tail, f, log_domain<MODE, FN>() ? R(neg_inf()) : R(0));
     acc.add(f);
     acc.flush();
-    acc.store_lane(partial + tile);
+    if (in_bounds(st, tile, cap_partial_sums(D), kSiteLaneSum)) acc.store_lane(partial + tile);
 }
 
 // One kernel per dimension DIM: each holds only the sample loop its d needs.
@@ -585,23 +586,24 @@ zmc_eval_reduce(const Desc* __restrict__ desc, State* st,
     if (tid < 4) s_c[tid] = (R)D.c[tid];
     __syncthreads();
 
-    const UnitPlan plan = unit_plan<MODE>(D, C);
+    const UnitPlan plan = st->uplan[level];
     const UnitQueue queue(st, level);
     double2* slot = &s_acc[MODE == ZMC_FP32_FP64ACC ? tid : 0];
     for (int64_t u = queue.first(); u < plan.units; u = queue.next()) {
         if (plan.lane_tiles) {
             lane_tile_unit<MODE, FN, DIM>(D, level, plan, u, parents, keys, s_coef[warp],
-                                          s_lane_beta[warp], s_pb, s_c, slot, partial);
+                                          s_lane_beta[warp], s_pb, s_c, slot, partial, st);
             __syncwarp();
             continue;
         }
         const Unit un = unit_of(plan, u);
-        const R start = fold_setup<MODE, FN>(D, level, un.q, parents, s_coef[warp], s_term[warp]);
+        const R start =
+            fold_setup<MODE, FN>(D, level, un.q, parents, s_coef[warp], s_term[warp], st);
         const StreamConst sc = stream_const(keys, un.t, (uint32_t)un.q, (uint32_t)level);
         SumsFor<MODE, FN> acc(slot, value_scale<MODE, FN>(D));
         sample_unit_fold<MODE, FN, DIM>(acc, keys, sc, s_coef[warp], s_pb, s_c, start, un.g0,
                                         un.g1, plan.ngroups - 1, plan.tail);
-        acc.reduce_store(partial + u);
+        if (in_bounds(st, u, cap_partial_sums(D), kSiteUnitSum)) acc.reduce_store(partial + u);
         __syncwarp();   // the warp's coefficient slice is rewritten by the next unit
     }
 }
@@ -631,7 +633,7 @@ __device__ __forceinline__ void eval_expr_body(const Desc* __restrict__ desc,
     if (tid < 4) s_p[2 * ZMC_MAX_DIM + tid] = (R)D.c[tid];
     __syncthreads();
 
-    const UnitPlan plan = unit_plan<MODE>(D, C, false);
+    const UnitPlan plan = st->uplan[level];
     const UnitQueue queue(st, level);
     double2* slot = &s_acc[MODE == ZMC_FP32_FP64ACC ? tid : 0];
     R2* wb = s_wb[warp];
@@ -641,26 +643,58 @@ __device__ __forceinline__ void eval_expr_body(const Desc* __restrict__ desc,
         if (lane < DIM) {
             const double w = D.width[level][lane];
             wb[lane].x = (R)w;
-            wb[lane].y = (R)cell_shift<MODE>(D, level, un.q, lane, parents, w);
+            wb[lane].y = (R)cell_shift<MODE>(D, level, un.q, lane, parents, w, st);
         }
         __syncwarp();
         const StreamConst sc = stream_const(keys, un.t, (uint32_t)un.q, (uint32_t)level);
         LaneSums<MODE> acc(slot);
-        // the G points of group gg: coordinates from the blocks, then E
+        // the G points of group gg: coordinates from the blocks, then E.  An
+        // FP32 group is evaluated in two halves (points 0..4 from each
+        // dimension's first block, then 5..10 from its second block and the
+        // pair's cross field), so only six points' coordinates are live.
         auto values = [&](uint32_t gg, R (&f)[G]) {
-            R x[G][DIM];
-            const uint32_t cbase = gg * DIM;
+            if constexpr (MODE == ZMC_FP64) {
+                R x[G][DIM];
+                const uint32_t cbase = gg * DIM;
 #pragma unroll
-            for (int i = 0; i < DIM; ++i) {
-                const uint4 w = philox_stream(keys, sc, cbase + i);
-                const R2 c = wb[i];
-                R v[G];
-                block_points<MODE>(w, v);
+                for (int i = 0; i < DIM; ++i) {
+                    const uint4 w = philox_stream(keys, sc, cbase + i);
+                    const R2 c = wb[i];
+                    R v[G];
+                    block_points<MODE>(w, w, v);
 #pragma unroll
-                for (int p = 0; p < G; ++p) x[p][i] = fma(v[p], c.x, c.y);
+                    for (int p = 0; p < G; ++p) x[p][i] = fma(v[p], c.x, c.y);
+                }
+#pragma unroll
+                for (int p = 0; p < G; ++p) f[p] = E::eval(x[p], s_p);
+            } else {
+                R x[6][DIM];
+                uint4 first[DIM];
+                const uint32_t cbase = 2 * gg * DIM;
+#pragma unroll
+                for (int i = 0; i < DIM; ++i) {
+                    first[i] = philox_stream(keys, sc, cbase + 2 * i);
+                    const R2 c = wb[i];
+                    R v[5];
+                    fields_1m(first[i], v[0], v[1], v[2], v[3], v[4]);
+#pragma unroll
+                    for (int p = 0; p < 5; ++p) x[p][i] = fma(v[p], c.x, c.y);
+                }
+#pragma unroll
+                for (int p = 0; p < 5; ++p) f[p] = E::eval(x[p], s_p);
+#pragma unroll
+                for (int i = 0; i < DIM; ++i) {
+                    const uint4 w2 = philox_stream(keys, sc, cbase + 2 * i + 1);
+                    const R2 c = wb[i];
+                    R v[6];
+                    fields_1m(w2, v[0], v[1], v[2], v[3], v[4]);
+                    v[5] = cross_1m(first[i], w2);
+#pragma unroll
+                    for (int p = 0; p < 6; ++p) x[p][i] = fma(v[p], c.x, c.y);
+                }
+#pragma unroll
+                for (int p = 0; p < 6; ++p) f[5 + p] = E::eval(x[p], s_p);
             }
-#pragma unroll
-            for (int p = 0; p < G; ++p) f[p] = E::eval(x[p], s_p);
         };
         // as in sample_unit_fold: the tile's last group, the only one that
         // can run past n, is left to the one lane it falls to
@@ -682,7 +716,7 @@ __device__ __forceinline__ void eval_expr_body(const Desc* __restrict__ desc,
             acc.add(f);
             acc.flush();
         }
-        acc.reduce_store(partial + u);
+        if (in_bounds(st, u, cap_partial_sums(D), kSiteUnitSum)) acc.reduce_store(partial + u);
         __syncwarp();
     }
 }
@@ -711,19 +745,29 @@ inline const void* eval_kernel_dim(int d) {
     default: return nullptr;
     }
 }
-template <int MODE>
-inline const void* eval_kernel_for(int fn, int d) {
-    switch (fn) {
-    case kConstant: return eval_kernel_dim<MODE, kConstant>(d);
-    case kLinear: return eval_kernel_dim<MODE, kLinear>(d);
-    case kSinSum: return eval_kernel_dim<MODE, kSinSum>(d);
-    case kGaussNorm: return eval_kernel_dim<MODE, kGaussNorm>(d);
-    case kGenzOsc: return eval_kernel_dim<MODE, kGenzOsc>(d);
-    case kGenzProdPeak: return eval_kernel_dim<MODE, kGenzProdPeak>(d);
-    case kGenzGauss: return eval_kernel_dim<MODE, kGenzGauss>(d);
-    case kGenzCorner: return eval_kernel_dim<MODE, kGenzCorner>(d);
-    default: return nullptr;
+// The registry kernels of one precision mode are compiled in four parts,
+// translation units that the build generates (build.py): part p holds
+// integrands 2p and 2p + 1 of the registry order, so the parts compile in
+// parallel.  The bounds-guarded test build compiles sin_sum and genz_corner
+// only.
+template <int FN>
+constexpr bool in_build() {
+#ifdef ZMC_CHECKED
+    return FN == kSinSum || FN == kGenzCorner;
+#else
+    return true;
+#endif
+}
+template <int MODE, int PART>
+inline const void* eval_kernel_pair(int fn, int d) {
+    constexpr int F0 = 2 * PART, F1 = 2 * PART + 1;
+    if constexpr (in_build<F0>()) {
+        if (fn == F0) return eval_kernel_dim<MODE, F0>(d);
     }
+    if constexpr (in_build<F1>()) {
+        if (fn == F1) return eval_kernel_dim<MODE, F1>(d);
+    }
+    return nullptr;
 }
 #endif
 

@@ -164,8 +164,13 @@ int nvrtc_cubin(const std::string& e, int dim, int mode, int major, int minor,
         return ZMC_ERR_COMPILE;
     }
     const std::string arch = "-arch=sm_" + std::to_string(major * 10 + minor) + (major >= 9 ? "a" : "");
+#ifdef ZMC_CHECKED
+    const char* opts[] = {arch.c_str(), "-std=c++17", "-default-device", "-lineinfo",
+                          "-DZMC_CHECKED"};
+#else
     const char* opts[] = {arch.c_str(), "-std=c++17", "-default-device", "-lineinfo"};
-    r = g_nvrtc.compile(prog, 4, opts);
+#endif
+    r = g_nvrtc.compile(prog, (int)(sizeof opts / sizeof opts[0]), opts);
     size_t ls = 0;
     g_nvrtc.log_size(prog, &ls);
     std::string clog(ls, '\0');

@@ -129,12 +129,17 @@ __device__ bool last_to_arrive(uint32_t* ticket) {
 // Each step below is a device body run by one grid (or, for a batch of
 // integrals, by row blockIdx.y of a 2-D grid) and a thin kernel around it.
 
-// Reset the tree state of a run: level 1 is the full lattice.
-__device__ __forceinline__ void init_state_body(State* st, int64_t level1_cells) {
+// Reset the tree state of a run: level 1 is the full lattice, with its work
+// decomposition.
+__device__ __forceinline__ void init_state_body(const Desc* __restrict__ desc, State* st,
+                                                int64_t level1_cells) {
     uint32_t* w = reinterpret_cast<uint32_t*>(st);
     for (size_t i = threadIdx.x; i < sizeof(State) / 4; i += blockDim.x) w[i] = 0u;
     __syncthreads();
-    if (threadIdx.x == 0) st->cells[1] = level1_cells;
+    if (threadIdx.x == 0) {
+        st->cells[1] = level1_cells;
+        st->uplan[1] = level_plan(*desc, level1_cells);
+    }
 }
 
 // Step (b1): per cell the mean and sample spread (ddof 1) of the trial
@@ -153,13 +158,16 @@ __device__ __forceinline__ void cell_stats_body(const Desc* __restrict__ desc, S
     int64_t begin, end;
     chunk_of(C, begin, end);
 
-    // The sampling kernel left unit_chunks() partial sums per (cell, trial)
-    // tile, contiguous per tile; add them in order and keep the total in the
-    // tile's first slot.
-    const int64_t chunks = unit_chunks(C * T, groups_of(D.n, D.mode), D.plan);
+    // The sampling kernel left the level plan's `chunks` partial sums per
+    // (cell, trial) tile, contiguous per tile; add them in order and keep the
+    // total in the tile's first slot.
+    const int64_t chunks = st->uplan[level].chunks;
     bool finite = true;
     Moments acc{0.0, 0.0, 0.0};
     for (int64_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
+        if (!in_bounds(st, (q + 1) * T * chunks - 1, cap_partial_sums(D), kSiteSumsRead) ||
+            !in_bounds(st, q, D.cap_cells, kSiteStatsWrite))
+            continue;
         double2* row = sums + q * T * chunks;
         if (chunks > 1) {
             for (int t = 0; t < T; ++t) {
@@ -231,6 +239,7 @@ __device__ __forceinline__ void flag_count_body(const Desc* __restrict__ desc, S
     int64_t cnt = 0;
     double mm = INFINITY;
     for (int64_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
+        if (!in_bounds(st, q, D.cap_cells, kSiteStatsRead)) continue;
         const double s = cell_stats[q].y;
         cnt += (can_flag && s > theta) ? 1 : 0;
         if (theta > 0.0) mm = fmin(mm, fabs(s - theta) / theta);
@@ -280,6 +289,7 @@ __device__ __forceinline__ void flag_count_body(const Desc* __restrict__ desc, S
             } else {
                 refine = 1;
                 st->cells[level + 1] = (int64_t)next;
+                st->uplan[level + 1] = level_plan(D, (int64_t)next);
             }
         }
         st->flagged[level] = flagged;
@@ -319,7 +329,7 @@ __device__ __forceinline__ void compact_body(const Desc* __restrict__ desc,
     CSum val{0.0, 0.0}, var{0.0, 0.0};
     for (int64_t q0 = begin; q0 < end; q0 += blockDim.x) {
         const int64_t q = q0 + threadIdx.x;
-        const bool valid = q < end;
+        const bool valid = q < end && in_bounds(st, q, D.cap_cells, kSiteStatsRead);
         double2 ms = valid ? cell_stats[q] : make_double2(0.0, 0.0);
         const bool flag = valid && refine && ms.y > theta;
         const unsigned ballot = __ballot_sync(0xFFFFFFFFu, flag);
@@ -334,8 +344,10 @@ __device__ __forceinline__ void compact_body(const Desc* __restrict__ desc,
         __syncthreads();
         if (flag) {
             const int64_t r = offset + s_warp[warp] + rank_in_warp;
-            for (int i = 0; i < d; ++i)
-                parents_next[r * d + i] = (uint32_t)cell_coord(D, level, q, i, parents_prev);
+            if (in_bounds(st, r * d + d - 1, cap_parents(D), kSiteParentWrite))
+                for (int i = 0; i < d; ++i)
+                    parents_next[r * d + i] =
+                        (uint32_t)cell_coord(D, level, q, i, parents_prev, st);
         } else if (valid) {
             val.add(ms.x);
             var.add(ms.y * ms.y / T);
@@ -390,8 +402,8 @@ __device__ __forceinline__ void final_body(const State* __restrict__ st,
 
 // ---------------------------------------------------------------- kernels
 // One integration: the buffers are kernel arguments.
-__global__ void zmc_init_state(State* st, int64_t level1_cells) {
-    init_state_body(st, level1_cells);
+__global__ void zmc_init_state(const Desc* desc, State* st, int64_t level1_cells) {
+    init_state_body(desc, st, level1_cells);
 }
 __global__ void __launch_bounds__(kSelThreads)
 zmc_cell_stats(const Desc* desc, State* st, double2* sums, double2* cell_stats, double* part,
@@ -417,7 +429,7 @@ zmc_final(const State* st, const double* part_acc, int sel_grid, zmc_result* out
 // A batch of integrations: row blockIdx.y of the grid works on items[y].
 // Level L reads the parent list written by level L-1 (ping-pong by parity).
 __global__ void zmc_init_state_batch(const Buffers* items, const int64_t* level1_cells) {
-    init_state_body(items[blockIdx.y].state, level1_cells[blockIdx.y]);
+    init_state_body(items[blockIdx.y].desc, items[blockIdx.y].state, level1_cells[blockIdx.y]);
 }
 __global__ void __launch_bounds__(kSelThreads)
 zmc_cell_stats_batch(const Buffers* items, int level) {
@@ -454,25 +466,30 @@ __global__ void zmc_philox_fill(const PhiloxKeys keys, uint32_t c0, uint32_t c1,
 
 // The uniforms of points [first, first + count) of one (level, slot, trial)
 // stream, all d dimensions, as the sampling kernel forms them (1.m values
-// from philox_stream, block_points' field layout), minus the exact shift.
+// from philox_stream with the word and field layout of the sampling loop),
+// minus the exact shift.
 __global__ void zmc_uniforms_fill(const PhiloxKeys keys, uint32_t level, uint32_t slot,
                                   uint32_t trial, int d, int mode, int64_t first, int64_t count,
                                   double* out) {
     const StreamConst sc = stream_const(keys, trial, slot, level);
-    const int G = mode == ZMC_FP64 ? 4 : 5;
+    const int G = points_per_group(mode), B = blocks_per_group(mode);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count * d;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = first + e / d;
         const int i = (int)(e % d);
-        const uint4 w = philox_stream(keys, sc, (uint32_t)((s / G) * d + i));
+        const uint32_t c0 = (uint32_t)(((s / G) * d + i) * B);
+        const uint4 w = philox_stream(keys, sc, c0);
         const int lane = (int)(s % G);
         double u;
         if (mode == ZMC_FP64) {
             const uint32_t word = lane == 0 ? w.x : lane == 1 ? w.y : lane == 2 ? w.z : w.w;
             u = one_plus_word_f64(word) - (1.0 - 0x1p-33);
         } else {
-            float v[5];
+            const uint4 w2 = philox_stream(keys, sc, c0 + 1);
+            float v[11];
             fields_1m(w, v[0], v[1], v[2], v[3], v[4]);
+            fields_1m(w2, v[5], v[6], v[7], v[8], v[9]);
+            v[10] = cross_1m(w, w2);
             u = (double)(v[lane] - (1.0f - 0x1p-24f));
         }
         out[e] = u;
@@ -504,7 +521,7 @@ PhiloxKeys philox_keys(uint64_t seed) {
 // ------------------------------------------------------------- launchers
 
 cudaError_t launch_init(const Buffers& b, int64_t level1_cells, cudaStream_t s) {
-    zmc_init_state<<<1, 256, 0, s>>>(b.state, level1_cells);
+    zmc_init_state<<<1, 256, 0, s>>>(b.desc, b.state, level1_cells);
     return cudaGetLastError();
 }
 

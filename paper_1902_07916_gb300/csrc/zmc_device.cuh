@@ -71,9 +71,16 @@ __device__ __forceinline__ uint4 philox_stream(const PhiloxKeys& K, const Stream
 }
 
 // ------------------------------------------------------ word -> point maps
-// The stream of (level L, slot q, trial t): dimension i of samples
-// G g .. G g + G - 1 is the block with counter (g*d + i, t, q, L); G = 4 in
-// the FP64 stream (one 32-bit word per sample), 5 in the FP32 stream.
+// The stream of (level L, slot q, trial t).  FP64 stream: dimension i of
+// samples 4g .. 4g + 3 are the four 32-bit words of the block with counter
+// (g*d + i, t, q, L).  FP32 stream: dimension i of samples 11g .. 11g + 10
+// come from the PAIR of blocks with counters (2(g*d + i), t, q, L) and
+// (2(g*d + i) + 1, t, q, L), each read as a 128-bit integer: samples 0..4 of
+// the group take the first block's 23-bit fields (bits 23f .. 23f + 22),
+// samples 5..9 the second block's, and sample 10 the 23-bit value made of the
+// first block's bits 115..127 (low 13 bits) and the second block's bits
+// 115..124 (high 10 bits) -- 253 of the pair's 256 bits, where five fields
+// per block used 230.
 //
 // FP64 stream: u = (w + 1/2) 2^-32.  The double 1 + w 2^-32 is assembled
 // from the word's bits, and the point lo + (c + u) w_L is formed from it as
@@ -81,9 +88,7 @@ __device__ __forceinline__ uint4 philox_stream(const PhiloxKeys& K, const Stream
 __device__ __forceinline__ double one_plus_word_f64(uint32_t w) {
     return __hiloint2double(0x3FF00000 | (int)(w >> 12), (int)(w << 20));
 }
-// FP32 stream: a block carries dimension i of FIVE points, as the 23-bit
-// fields f = 0..4 of the block read as a 128-bit integer (bits 23 f ..
-// 23 f + 22); u = (field + 1/2) 2^-23, exact in binary32.  The float
+// FP32 stream: u = (field + 1/2) 2^-23, exact in binary32.  The float
 // 1 + field 2^-23 is assembled from the bits, and the point is
 // w_L * (1.m) + (lo + c w_L - (1 - 2^-24) w_L).
 // One three-input LOP3, (field & 0x7FFFFF) | exponent, with the exponent
@@ -95,6 +100,7 @@ __device__ __forceinline__ float one_plus_field(uint32_t field23) {
     asm("lop3.b32 %0, %1, 0x7FFFFF, %2, 0xEA;" : "=r"(r) : "r"(field23), "r"(0x3F800000u));
     return __uint_as_float(r);
 }
+// The five 23-bit fields of one block.
 __device__ __forceinline__ void fields_1m(uint4 w, float& v0, float& v1, float& v2, float& v3,
                                           float& v4) {
     v0 = one_plus_field(w.x);                              // bits   0 ..  22
@@ -102,6 +108,12 @@ __device__ __forceinline__ void fields_1m(uint4 w, float& v0, float& v1, float& 
     v2 = one_plus_field(__funnelshift_r(w.y, w.z, 14));    // bits  46 ..  68
     v3 = one_plus_field(w.z >> 5);                         // bits  69 ..  91
     v4 = one_plus_field(__funnelshift_r(w.z, w.w, 28));    // bits  92 .. 114
+}
+// The pair's eleventh field: bits 115..127 of a (a.w >> 19) below bits
+// 115..124 of b (b.w bits 19..28, moved to bits 13..22).
+__device__ __forceinline__ float cross_1m(uint4 a, uint4 b) {
+    const uint32_t f = (a.w >> 19) | ((b.w >> 6) & 0x7FE000u);
+    return __uint_as_float(f | 0x3F800000u);
 }
 
 // ------------------------------------------------ elementary functions
@@ -241,16 +253,50 @@ template <typename R> struct Fn<kGenzCorner, R> {    // (1 + sum pa_i x_i)^-(d+1
     }
 };
 
+// ------------------------------------------------- bounds-guarded build
+// Compiled with ZMC_CHECKED (a test build of the library), every index into a
+// partial-sum, cell-statistics or parent-list buffer is checked against the
+// buffer's capacity before the access; a failed check records its site in
+// the tree state (the first to fail wins), raises the run's status to
+// ZMC_ERR_CHECK and skips the access, so a bad index shows up as a status
+// instead of a fault.  In the normal build the checks compile away.
+enum CheckSite : uint32_t {
+    kSiteUnitSum = 1,      // sampling kernel: a unit's (S1, S2) slot
+    kSiteLaneSum = 2,      // sampling kernel: a lane tile's slot
+    kSiteParentRead = 3,   // a parent's coordinates (deeper levels)
+    kSiteSumsRead = 4,     // statistics kernel: a cell's unit slots
+    kSiteStatsWrite = 5,   // statistics kernel: a cell's (mean, spread)
+    kSiteStatsRead = 6,    // flag and compaction kernels: a cell's statistics
+    kSiteParentWrite = 7,  // compaction kernel: a flagged cell's coordinates
+};
+
+__device__ __forceinline__ bool in_bounds(const State* st, int64_t idx, int64_t cap,
+                                          uint32_t site) {
+#ifdef ZMC_CHECKED
+    if (idx >= 0 && idx < cap) return true;
+    State* w = const_cast<State*>(st);
+    atomicCAS(&w->check_site, 0u, site);
+    atomicMax(&w->status, ZMC_ERR_CHECK);
+    return false;
+#else
+    (void)st; (void)idx; (void)cap; (void)site;
+    return true;
+#endif
+}
+
 // ------------------------------------------------------- cell geometry
 // Lattice coordinate (dimension i) of work-list slot q at `level`.  Level 1
 // is the full row-major lattice (dimension 0 fastest); at deeper levels slot
 // q is child (q mod K) of the (q div K)-th flagged cell of the previous
-// level, whose coordinates are in `parents` (flagged * d, uint32).
+// level, whose coordinates are in `parents` (flagged * d, uint32).  `st` is
+// the run's tree state, used by the bounds-guarded build only.
 __device__ __forceinline__ int64_t cell_coord(const Desc& D, int level, int64_t q,
-                                              int i, const uint32_t* parents) {
+                                              int i, const uint32_t* parents,
+                                              const State* st) {
     if (level == 1) return (q / D.kpow[i]) % D.k;
     const int64_t r = q / D.K;
     const int64_t digit = q - r * D.K;
+    if (!in_bounds(st, r * D.d + i, cap_parents(D), kSiteParentRead)) return 0;
     return (int64_t)D.k * parents[r * D.d + i] + (digit / D.kpow[i]) % D.k;
 }
 

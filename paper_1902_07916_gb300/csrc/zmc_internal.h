@@ -70,13 +70,28 @@ struct BatchEval {
     int32_t fn;
 };
 
+// Sampling kernels (single-integral and batched) of precision mode MODE for
+// registry integrands 2*PART and 2*PART + 1, by integrand id and dimension;
+// nullptr for any other integrand.  Each (MODE, PART) is one translation unit
+// generated by the build (eval_kernel_pair / batch_kernel_pair).
+template <int MODE, int PART> const void* eval_kernel_part(int fn, int d);
+template <int MODE, int PART> const void* batch_kernel_part(int fn, int d);
+#define ZMC_DECLARE_KERNEL_PART(M, P)                                   \
+    template <> const void* eval_kernel_part<M, P>(int fn, int d);      \
+    template <> const void* batch_kernel_part<M, P>(int fn, int d);
+#define ZMC_DECLARE_KERNEL_PARTS(M) \
+    ZMC_DECLARE_KERNEL_PART(M, 0) ZMC_DECLARE_KERNEL_PART(M, 1) \
+    ZMC_DECLARE_KERNEL_PART(M, 2) ZMC_DECLARE_KERNEL_PART(M, 3)
+ZMC_DECLARE_KERNEL_PARTS(ZMC_FP64)
+ZMC_DECLARE_KERNEL_PARTS(ZMC_FP32_FP64ACC)
+ZMC_DECLARE_KERNEL_PARTS(ZMC_FP32_KAHAN)
+#undef ZMC_DECLARE_KERNEL_PARTS
+#undef ZMC_DECLARE_KERNEL_PART
+constexpr int kKernelParts = 4;
+
 // Batched form (batch.cu, select.cu): `items` / `level1_cells` / `out` are
 // device arrays of `count` entries; row y of each selection grid works on
 // integral y.
-// Batched sampling kernels of one mode by integrand (eval_fp*.cu).
-const void* batch_kernel_fp64(int fn, int d);
-const void* batch_kernel_fp32_fp64acc(int fn, int d);
-const void* batch_kernel_fp32_kahan(int fn, int d);
 // Plan + sampling kernel of one group of `count` integrals (same integrand):
 // `offsets` has count + 1 entries, `head` is the group's queue counter.
 cudaError_t launch_batch_level(const BatchEval* items, int count, int level, int64_t* offsets,

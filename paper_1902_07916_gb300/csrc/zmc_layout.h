@@ -31,7 +31,7 @@ enum Integrand : int32_t {
 // units of about equal numbers of point groups so that a level has at least
 // target_units units when it can, but no unit has fewer than
 // min_unit_groups groups ("samples per thread": a lane takes one group in
-// 32 of its unit).  Lane tiles: a unit of 32 consecutive tiles, each lane one
+// 32 of its unit; a group is 4 points in FP64, 11 in the FP32 modes).  Lane tiles: a unit of 32 consecutive tiles, each lane one
 // whole tile, in place of one tile per warp (which leaves lanes idle on small
 // tiles and pays a per-tile set-up and FP64 warp reduction); taken for tiles
 // of fewer than lane_tile_groups point groups always, and for tiles of fewer
@@ -72,6 +72,15 @@ struct Desc {
     WorkPlan plan;                   // work decomposition of the sampling kernel
 };
 
+// Work decomposition of one level under the run's work plan: computed once,
+// by the kernel that sets the level's cell count (level_plan below), and read
+// by the sampling and statistics kernels.
+struct UnitPlan {
+    int64_t units, chunks, tiles;  // chunks: unit slots per tile (1 for lane tiles)
+    uint32_t ngroups, tail;        // point groups per tile; real points of the last
+    int32_t T, lane_tiles;         // trials; a unit is 32 tiles, one per lane
+};
+
 // Tree state of one run, written only by the kernels.  Index L = level.
 struct State {
     int64_t cells[ZMC_MAX_DEPTH + 2];
@@ -85,6 +94,8 @@ struct State {
     int32_t status;      // ZMC_OK or a ZMC_ERR_* code
     int32_t levels_run;
     uint32_t ticket[4];  // last-block arrival counters (self-resetting)
+    uint32_t check_site; // bounds-guarded build: first failing check (0: none)
+    UnitPlan uplan[ZMC_MAX_DEPTH + 2];            // work decomposition per level
     unsigned long long queue[ZMC_MAX_DEPTH + 2];  // sampling units taken per level
 };
 
@@ -95,20 +106,38 @@ struct State {
 constexpr int64_t kTargetUnits = int64_t(1) << 18;
 constexpr WorkPlan kDefaultPlan = {kTargetUnits, 1024, 64, 1024, int64_t(1) << 18};
 
-// Points per Philox block in the mode's stream: four 32-bit words (FP64) or
-// five 23-bit fields (FP32 modes); a "group" is that many consecutive points.
+// A point "group" of the mode's stream: four points from one Philox block
+// per dimension (FP64: its 32-bit words) or eleven from a pair of blocks
+// (FP32 modes: 23-bit fields, see zmc_device.cuh).
 #ifdef __CUDACC__
 __host__ __device__
 #endif
-inline int points_per_block(int mode) { return mode == ZMC_FP64 ? 4 : 5; }
+inline int points_per_group(int mode) { return mode == ZMC_FP64 ? 4 : 11; }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int blocks_per_group(int mode) { return mode == ZMC_FP64 ? 1 : 2; }
 
 #ifdef __CUDACC__
 __host__ __device__
 #endif
 inline int64_t groups_of(int64_t n, int mode) {
-    const int G = points_per_block(mode);
+    const int G = points_per_group(mode);
     return (n + G - 1) / G;
 }
+
+// Capacities of a handle's per-level buffers, in elements: unit partial
+// sums (a level of `tiles` tiles has at most tiles + target_units <=
+// tiles + kTargetUnits units), cell statistics, and each parent list
+// (flagged cells x d coordinates).
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int64_t cap_partial_sums(const Desc& D) { return D.cap_cells * D.T + kTargetUnits; }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int64_t cap_parents(const Desc& D) { return (D.cap_cells / D.K + 1) * D.d; }
 
 #ifdef __CUDACC__
 __host__ __device__
@@ -137,6 +166,25 @@ inline int64_t level_units(int64_t tiles, int64_t ngroups, bool allow_lane_tiles
                            const WorkPlan& w) {
     if (allow_lane_tiles && lane_tiles(tiles, ngroups, w)) return (tiles + 31) / 32;
     return tiles * unit_chunks(tiles, ngroups, w);
+}
+
+// The work decomposition of a level of C cells.  Lane tiles write one slot
+// per tile, so their chunk count is 1 whatever unit_chunks says; registry
+// integrands may use lane tiles, expressions never do.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline UnitPlan level_plan(const Desc& D, int64_t C) {
+    UnitPlan p;
+    p.T = D.T;
+    p.ngroups = (uint32_t)groups_of(D.n, D.mode);           // < 2^32: n * d < 2^34
+    p.tail = (uint32_t)(D.n - (int64_t)points_per_group(D.mode) * (int64_t)(p.ngroups - 1));
+    p.tiles = C * D.T;
+    const bool allow = D.integrand != kExpression;
+    p.lane_tiles = (allow && lane_tiles(p.tiles, p.ngroups, D.plan)) ? 1 : 0;
+    p.chunks = p.lane_tiles ? 1 : unit_chunks(p.tiles, p.ngroups, D.plan);
+    p.units = level_units(p.tiles, p.ngroups, allow, D.plan);
+    return p;
 }
 
 }  // namespace zmc

@@ -17,7 +17,9 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libzmc.so")
+# ZMC_LIBRARY selects another build of the library (the bounds-guarded test
+# build, _build_checked/libzmc.so); the default is the in-tree build.
+LIB_PATH = os.environ.get("ZMC_LIBRARY") or os.path.join(_HERE, "_build", "libzmc.so")
 
 ZMC_OK = 0
 ZMC_ERR_ARG = 1
@@ -28,6 +30,7 @@ ZMC_ERR_OOM = 5
 ZMC_ERR_CUDA = 6
 ZMC_ERR_TIMEOUT = 7
 ZMC_ERR_NOINTEGRAND = 8
+ZMC_ERR_CHECK = 9
 
 ZMC_FP64 = 0
 ZMC_FP32_FP64ACC = 1

@@ -33,13 +33,24 @@ def test_median_first():
 
 
 def test_algorithmic_bytes_of_the_benchmark_step():
-    # sin6d: level 1 has 4096 x 10 tiles of 13108 point groups, cut into
-    # ceil(2^18 / 40960) = 7 units each; level 2 has 1,204,224 x 10 tiles, one
-    # unit each; 16 bytes per unit, averaged over the two launches
-    level1 = 4096 * 10 * 7 * 16
+    # sin6d, FP32 stream: level 1 has 4096 x 10 tiles of ceil(65536 / 11) =
+    # 5958 point groups, cut into min(ceil(2^18 / 40960), 5958 // 1024) = 5
+    # units each; level 2 has 1,204,224 x 10 tiles, one unit each; 16 bytes
+    # per unit, averaged over the two launches
+    level1 = 4096 * 10 * 5 * 16
     level2 = 1204224 * 10 * 16
     got = bench.algorithmic_bytes_per_launch([4096, 1204224], 1 << 16, 10, False)
-    assert got == (level1 + level2) / 2 == 98631680
+    assert got == (level1 + level2) / 2 == 97976320
+    # the FP64 stream: 16384 groups of 4, 7 units per level-1 tile
+    got64 = bench.algorithmic_bytes_per_launch([4096], 1 << 16, 10, True)
+    assert got64 == 4096 * 10 * 7 * 16
+
+
+def test_philox_work_per_point():
+    # 17 wide multiplies per block; FP64: 1 block per 4 points per dimension,
+    # FP32: 2 blocks per 11 points per dimension
+    assert bench.philox_multiplies_per_sample(6, True) == 6 * 17 / 4
+    assert bench.philox_multiplies_per_sample(6, False) == pytest.approx(6 * 34 / 11, rel=1e-15)
 
 
 def test_fp32_flop_counts():

@@ -61,7 +61,8 @@ def test_philox_words_bit_exact(zmc, seed, ctr):
     (2**64 - 1, 4, 2**32 - 1, 2**32 - 1, 16, 1001, 64), (7, 3, 5, 1, 9, 0, 5),
 ])
 def test_uniforms_bit_exact(zmc, mode, seed, level, slot, trial, dim, first, count):
-    # both streams (four 32-bit words / five 23-bit fields per block), for
+    # both streams (four 32-bit words per block / eleven 23-bit fields per
+    # pair of blocks), for
     # ragged starting points and every dimension, against the oracle
     import torch
     out = torch.full((count * dim,), float("nan"), dtype=torch.float64, device="cuda")

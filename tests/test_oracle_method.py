@@ -261,7 +261,7 @@ def test_budget_accepts_level_whole(oracle):
 
 
 def test_fp32_stream_is_an_independent_estimate(oracle):
-    # The FP32 stream samples other points (five 23-bit fields per block):
+    # The FP32 stream samples other points (eleven 23-bit fields per pair of blocks):
     # both estimates agree with the closed form and with each other within
     # their errors.
     args = (3, [0.0] * 3, [10.0] * 3, 4, 2000, 5, 1, 2.0, 0, "sin_sum")

@@ -114,16 +114,34 @@ def test_field_uniform_exact_and_open(oracle, field):
     assert float(np.float32(u)) == u          # exactly representable in binary32
 
 
+@pytest.mark.parametrize("a,b", [((0, 0, 0, 0), (0xFFFFFFFF,) * 4),
+                                 ((0xFFFFFFFF,) * 4, (0, 0, 0, 0)),
+                                 ((0x12345678, 0x9ABCDEF0, 0x0F1E2D3C, 0x4B5A6978),
+                                  (0xDEADBEEF, 0x01234567, 0x89ABCDEF, 0xFEDCBA98))])
+def test_pair_field_is_the_two_blocks_slices(oracle, a, b):
+    # fields 0..4 from the first block's 128-bit integer, 5..9 from the
+    # second's, 10 = bits 115..127 of the first + 2^13 * bits 115..124 of the
+    # second: 253 of the pair's 256 bits, each used once
+    A = sum(int(w) << (32 * j) for j, w in enumerate(a))
+    B = sum(int(w) << (32 * j) for j, w in enumerate(b))
+    m23 = (1 << 23) - 1
+    want = [(A >> (23 * f)) & m23 for f in range(5)] + [(B >> (23 * f)) & m23 for f in range(5)]
+    want.append((A >> 115) + (((B >> 115) & 0x3FF) << 13))
+    assert [oracle.pair_field(a, b, f) for f in range(11)] == want
+
+
 def test_fp32_stream_layout(oracle):
-    # point s, dimension i of the FP32 stream is field s % 5 of the block with
-    # counter ((s // 5) * d + i, trial, slot, level)
+    # point s, dimension i of the FP32 stream is field s % 11 of the pair of
+    # blocks with counters (2 ((s // 11) * d + i) + {0, 1}, trial, slot, level)
     seed, level, slot, trial, d = 0x5EED, 2, 41, 3, 3
-    u = oracle.stream_uniforms(seed, level, slot, trial, d, True, 7, 12)
+    u = oracle.stream_uniforms(seed, level, slot, trial, d, True, 7, 30)
     key = oracle.seed_key(seed)
-    for r, s in enumerate(range(7, 19)):
+    for r, s in enumerate(range(7, 37)):
         for i in range(d):
-            blk = oracle.philox4x32_10(((s // 5) * d + i, trial, slot, level), key)
-            assert u[r, i] == oracle.field_uniform(oracle.field23(blk, s % 5))
+            c0 = 2 * ((s // 11) * d + i)
+            a = oracle.philox4x32_10((c0, trial, slot, level), key)
+            b = oracle.philox4x32_10((c0 + 1, trial, slot, level), key)
+            assert u[r, i] == oracle.field_uniform(oracle.pair_field(a, b, s % 11))
     # and the FP64 stream reads whole words, four points per block
     u64 = oracle.stream_uniforms(seed, level, slot, trial, d, False, 7, 12)
     w = oracle.stream_words(seed, level, slot, trial, d, 7, 12)
