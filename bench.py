@@ -246,8 +246,8 @@ def algorithmic_bytes_per_launch(cells_per_level, n, trials, fp64):
 # kernel's sources it was taken on (profiles/zmc_eval_reduce_sin6d_traffic.md).
 TRAFFIC_CAPTURE = {
     "workload": "sin6d", "fp64": False,
-    "bytes_per_launch": (72704 + 0 + 11275776 + 171680768) / 2,
-    "sources_sha256": "478a7e8ac92d7aea7367a779c70d0c2ef9ca931af83dc630af083a61a4f75f38",
+    "bytes_per_launch": (93440 + 0 + 11164160 + 181925376) / 2,
+    "sources_sha256": "cdf82dc5d66c7e005b62bccc26f62e5a8692cc4cc96c81aa459ac2ddd52dd61f",
 }
 KERNEL_SOURCES = ["eval_kernel.cuh", "zmc_device.cuh", "zmc_layout.h"]
 
