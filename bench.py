@@ -74,6 +74,8 @@ def parse():
     p.add_argument("--batch-level1", action="store_true",
                    help="--batch-compare with level-1-only budgets and no single runs "
                         "(a small case for ncu)")
+    p.add_argument("--no-singles", action="store_true",
+                   help="--batch-compare without the one-by-one runs (launch lists)")
     return p.parse_args()
 
 
@@ -1024,8 +1026,11 @@ def run_batch_compare(args):
         tb = min(times)
         out = {"integrals": len(ws), "precision": args.precision,
                "batch_s": round(tb, 4), "batch_gsamples_s": round(
-                   sum(r.samples for r in res) / tb / 1e9, 2)}
-        if args.batch_level1:
+                   sum(r.samples for r in res) / tb / 1e9, 2),
+               "cells_per_level": [sum(int(r.cells_per_level[L]) for r in res
+                                       if L < len(r.cells_per_level))
+                                   for L in range(max(w.depth for w in ws))]}
+        if args.batch_level1 or args.no_singles:
             return out
         single = []
         for w, h in zip(ws, hs):

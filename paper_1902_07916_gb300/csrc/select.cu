@@ -113,15 +113,72 @@ __device__ __forceinline__ void chunk_of(int64_t C, int64_t& begin, int64_t& end
     if (begin > C) begin = C;
 }
 
-// True in every thread of the CTA that arrived last at `ticket`.  The
-// caller's global writes are fenced before arriving.
-__device__ bool last_to_arrive(uint32_t* ticket) {
+// True in every thread of the CTA that arrived last at `ticket`, among
+// `ctas` arriving CTAs (the whole grid by default).  The caller's global
+// writes are fenced before arriving.
+__device__ bool last_to_arrive(uint32_t* ticket, unsigned ctas) {
     __shared__ bool last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == ctas - 1);
     __syncthreads();
     return last;
+}
+__device__ bool last_to_arrive(uint32_t* ticket) { return last_to_arrive(ticket, gridDim.x); }
+
+// RN(a / b) for b > 0 from rb = RN(1 / b) with one multiply and two FMAs:
+// q0 = RN(a rb) lies within one ulp of a / b, the remainder a - q0 b is then
+// exact in an FMA, and one correction step q0 + (a - q0 b) rb rounds to the
+// correctly rounded quotient (Markstein's theorem on division with a
+// correctly rounded reciprocal, IBM J. Res. Dev. 34(1), 1990).  Zero, tiny
+// (remainder near the subnormal range) and non-finite quotients take the
+// plain division.
+__device__ __forceinline__ double div_rn(double a, double b, double rb) {
+    const double q0 = a * rb;
+    if (!(fabs(q0) >= 0x1p-960 && fabs(q0) <= DBL_MAX)) return a / b;
+    return fma(fma(-q0, b, a), rb, q0);
+}
+
+// How many CTAs of the (fixed) grid take part in a selection step over
+// `work` units, at least `per_cta` units each: CTAs beyond that would only
+// add block reductions.  A function of the level's size only, so the
+// reduction order, and every bit of the result, stays the same on any GPU.
+constexpr int64_t kStatsWorkPerCta = 4096;   // (cell, trial) partial sums
+constexpr int64_t kCellsPerCta = 1024;       // cells, for flag and compaction
+__device__ __forceinline__ int active_ctas(int64_t work, int64_t per_cta) {
+    const int64_t g = (work + per_cta - 1) / per_cta;
+    return (int)(g < 1 ? 1 : (g < (int64_t)gridDim.x ? g : (int64_t)gridDim.x));
+}
+// The contiguous chunk of C cells owned by CTA blockIdx.x of G.
+__device__ __forceinline__ void chunk_of(int64_t C, int G, int64_t& begin, int64_t& end) {
+    const int64_t chunk = (C + G - 1) / G;
+    begin = (int64_t)blockIdx.x * chunk;
+    end = begin + chunk < C ? begin + chunk : C;
+    if (begin > C) begin = C;
+}
+
+// Sums of two doubles over the CTA in a fixed order (lane butterfly, then
+// the warps in order), returned to every thread.
+__device__ double2 block_sum2(double a, double b) {
+    __shared__ double2 s[32];
+    __shared__ double2 total;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s[warp] = make_double2(a, b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double2 t = make_double2(0.0, 0.0);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t.x += s[w].x;
+            t.y += s[w].y;
+        }
+        total = t;
+    }
+    __syncthreads();
+    const double2 r = total;
+    __syncthreads();
+    return r;
 }
 
 }  // namespace
@@ -144,7 +201,14 @@ __device__ __forceinline__ void init_state_body(const Desc* __restrict__ desc, S
 
 // Step (b1): per cell the mean and sample spread (ddof 1) of the trial
 // estimates I_{c,t} = V S1 / n; over the level the mean mu and population
-// standard deviation sigma of the spreads; theta = mu + m sigma.
+// standard deviation sigma of the spreads; theta = mu + m sigma.  FP64 runs
+// at two operations per SM per clock on GB300, so the kernel keeps FP64
+// divisions out of its loops: I_{c,t} and the mean are correctly rounded
+// quotients from precomputed reciprocals (div_rn; the same bits as a
+// division, so a cell whose trials agree has spread 0 exactly), and the
+// moments of the spreads are taken in two passes with plain sums -- per CTA
+// over its cells, then over the CTAs' (count, mean, M2) -- instead of
+// pairwise merges.
 __device__ __forceinline__ void cell_stats_body(const Desc* __restrict__ desc, State* st,
                                                 double2* __restrict__ sums,
                                                 double2* __restrict__ cell_stats, double* part,
@@ -153,17 +217,19 @@ __device__ __forceinline__ void cell_stats_body(const Desc* __restrict__ desc, S
     const int64_t C = st->cells[level];
     if (C <= 0) return;
     const int T = D.T;
-    const double V = D.volume[level];
-    const double n = (double)D.n;
-    int64_t begin, end;
-    chunk_of(C, begin, end);
-
     // The sampling kernel left the level plan's `chunks` partial sums per
     // (cell, trial) tile, contiguous per tile; add them in order and keep the
     // total in the tile's first slot.
     const int64_t chunks = st->uplan[level].chunks;
+    const int G = active_ctas(C * T * chunks, kStatsWorkPerCta);
+    if ((int)blockIdx.x >= G) return;
+    const double V = D.volume[level], n = (double)D.n, Td = (double)T;
+    const double rn = 1.0 / n, rT = 1.0 / Td, inv_T1 = 1.0 / (T - 1);
+    int64_t begin, end;
+    chunk_of(C, G, begin, end);
+
     bool finite = true;
-    Moments acc{0.0, 0.0, 0.0};
+    double tsum = 0.0, tcount = 0.0;
     for (int64_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
         if (!in_bounds(st, (q + 1) * T * chunks - 1, cap_partial_sums(D), kSiteSumsRead) ||
             !in_bounds(st, q, D.cap_cells, kSiteStatsWrite))
@@ -183,37 +249,61 @@ __device__ __forceinline__ void cell_stats_body(const Desc* __restrict__ desc, S
         // overflow in the FP32 modes when |f| exceeds ~1.8e19.
         double s = 0.0;
         for (int t = 0; t < T; ++t) {
-            const double2 S = row[t * chunks];
-            finite = finite && isfinite(S.x);
-            s += V * S.x / n;
+            const double S1 = row[t * chunks].x;
+            finite = finite && isfinite(S1);
+            s += div_rn(V * S1, n, rn);
         }
-        const double mean = s / T;
+        const double mean = div_rn(s, Td, rT);
         double ss = 0.0;
         for (int t = 0; t < T; ++t) {
-            const double e = V * row[t * chunks].x / n - mean;
-            ss += e * e;
+            const double e = div_rn(V * row[t * chunks].x, n, rn) - mean;
+            ss = fma(e, e, ss);
         }
-        const double spread = sqrt(ss / (T - 1));
+        const double spread = sqrt(ss * inv_T1);
         cell_stats[q] = make_double2(mean, spread);
-        acc = merge(acc, Moments{1.0, spread, 0.0});
+        tsum += spread;
+        tcount += 1.0;
     }
     if (!finite) atomicMax(&st->status, ZMC_ERR_NONFINITE);
-    acc = block_merge(acc);
-    if (threadIdx.x == 0) {
-        part[3 * blockIdx.x + 0] = acc.n;
-        part[3 * blockIdx.x + 1] = acc.mean;
-        part[3 * blockIdx.x + 2] = acc.m2;
+    // this CTA's count, mean and M2 of its spreads (the second pass reads
+    // back what this thread wrote)
+    const double2 sc = block_sum2(tsum, tcount);
+    const double cmean = sc.y > 0.0 ? sc.x / sc.y : 0.0;
+    double m2 = 0.0;
+    for (int64_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
+        if (!in_bounds(st, (q + 1) * T * chunks - 1, cap_partial_sums(D), kSiteSumsRead) ||
+            !in_bounds(st, q, D.cap_cells, kSiteStatsWrite))
+            continue;
+        const double e = cell_stats[q].y - cmean;
+        m2 = fma(e, e, m2);
     }
-    if (!last_to_arrive(&st->ticket[0])) return;
-
-    Moments all{0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-        all = merge(all, Moments{__ldcg(part + 3 * b), __ldcg(part + 3 * b + 1),
-                                 __ldcg(part + 3 * b + 2)});
-    all = block_merge(all);
+    const double m2c = block_sum2(m2, 0.0).x;
     if (threadIdx.x == 0) {
-        const double mu = all.mean;
-        const double sigma = sqrt(all.m2 / all.n);
+        part[3 * blockIdx.x + 0] = sc.y;
+        part[3 * blockIdx.x + 1] = cmean;
+        part[3 * blockIdx.x + 2] = m2c;
+    }
+    if (!last_to_arrive(&st->ticket[0], G)) return;
+
+    // The level's moments from the CTAs': mu = sum n_b mean_b / N and
+    // M2 = sum (M2_b + n_b (mean_b - mu)^2).
+    double a = 0.0, nn = 0.0;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) {
+        const double nb = __ldcg(part + 3 * b);
+        a += nb * __ldcg(part + 3 * b + 1);
+        nn += nb;
+    }
+    const double2 an = block_sum2(a, nn);
+    const double mu = an.y > 0.0 ? an.x / an.y : 0.0;
+    double m2g = 0.0;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) {
+        const double nb = __ldcg(part + 3 * b);
+        const double e = __ldcg(part + 3 * b + 1) - mu;
+        m2g += __ldcg(part + 3 * b + 2) + nb * e * e;
+    }
+    m2g = block_sum2(m2g, 0.0).x;
+    if (threadIdx.x == 0) {
+        const double sigma = an.y > 0.0 ? sqrt(m2g / an.y) : 0.0;
         st->mu[level] = mu;
         st->sigma[level] = sigma;
         st->theta[level] = mu + D.m * sigma;
@@ -233,16 +323,22 @@ __device__ __forceinline__ void flag_count_body(const Desc* __restrict__ desc, S
     if (C <= 0) return;
     const double theta = st->theta[level];
     const bool can_flag = level < D.depth;
+    const int G = active_ctas(C, kCellsPerCta);
+    if ((int)blockIdx.x >= G) return;
     int64_t begin, end;
-    chunk_of(C, begin, end);
+    chunk_of(C, G, begin, end);
 
+    // The margin min |s - theta| / theta: a correctly rounded division by
+    // theta > 0 is monotone, so the CTAs keep min |s - theta| and the last
+    // one divides once, which gives the same bits as the minimum of the
+    // quotients.
     int64_t cnt = 0;
     double mm = INFINITY;
     for (int64_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
         if (!in_bounds(st, q, D.cap_cells, kSiteStatsRead)) continue;
         const double s = cell_stats[q].y;
         cnt += (can_flag && s > theta) ? 1 : 0;
-        if (theta > 0.0) mm = fmin(mm, fabs(s - theta) / theta);
+        mm = fmin(mm, fabs(s - theta));
     }
     __shared__ int64_t s_cnt[32];
     __shared__ double s_mm[32];
@@ -261,18 +357,42 @@ __device__ __forceinline__ void flag_count_body(const Desc* __restrict__ desc, S
         part_count[blockIdx.x] = c;
         part_margin[blockIdx.x] = m;
     }
-    if (!last_to_arrive(&st->ticket[1])) return;
+    if (!last_to_arrive(&st->ticket[1], G)) return;
 
-    // exclusive scan of the per-CTA counts (gridDim.x <= 32 * blockDim.x)
-    __shared__ int64_t s_off[kSelGrid];
+    // Exclusive scan of the per-CTA counts over the whole CTA: thread j takes
+    // a run of `per` consecutive CTAs' counts, the runs' totals are scanned
+    // across the warps, and each thread then writes its run's offsets.
+    const int per = (G + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int b0 = min(G, (int)threadIdx.x * per), b1 = min(G, b0 + per);
+    int64_t mine = 0;
+    double mloc = INFINITY;
+    for (int b = b0; b < b1; ++b) {
+        mine += __ldcg(part_count + b);
+        mloc = fmin(mloc, __ldcg(part_margin + b));
+    }
+    int64_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+        mloc = fmin(mloc, __shfl_xor_sync(0xFFFFFFFFu, mloc, o));
+    }
+    if (lane == 31) s_cnt[warp] = incl;
+    if (lane == 0) s_mm[warp] = mloc;
+    __syncthreads();
+    int64_t before = 0, run = 0;
+    double m = INFINITY;
+    for (int w = 0; w < nw; ++w) {
+        if (w < warp) before += s_cnt[w];
+        run += s_cnt[w];
+        m = fmin(m, s_mm[w]);
+    }
+    int64_t off = before + incl - mine;
+    for (int b = b0; b < b1; ++b) {
+        part_offset[b] = off;
+        off += __ldcg(part_count + b);
+    }
     if (threadIdx.x == 0) {
-        int64_t run = 0;
-        double m = INFINITY;
-        for (int b = 0; b < (int)gridDim.x; ++b) {
-            s_off[b] = run;
-            run += __ldcg(part_count + b);
-            m = fmin(m, __ldcg(part_margin + b));
-        }
         const int64_t F = run;
         const int64_t per_cell = D.n * (int64_t)D.T;
         const int64_t samples = st->samples + C * per_cell;
@@ -294,12 +414,11 @@ __device__ __forceinline__ void flag_count_body(const Desc* __restrict__ desc, S
         }
         st->flagged[level] = flagged;
         st->refine[level] = refine;
-        st->min_margin[level] = can_flag ? m : INFINITY;
+        st->min_margin[level] =
+            (can_flag && theta > 0.0 && m < INFINITY) ? m / theta : INFINITY;
         st->levels_run = level;
         st->ticket[1] = 0u;
     }
-    __syncthreads();
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) part_offset[b] = s_off[b];
 }
 
 // Step (b3): write the coordinates of the flagged cells, in slot order, as
@@ -318,9 +437,16 @@ __device__ __forceinline__ void compact_body(const Desc* __restrict__ desc,
     if (C <= 0) return;
     const bool refine = st->refine[level] != 0;
     const double theta = st->theta[level];
-    const int T = D.T, d = D.d;
+    const int d = D.d;
+    const int G = active_ctas(C, kCellsPerCta);
+    if ((int)blockIdx.x >= G) {
+        // the final reduction reads every CTA's slot
+        if (threadIdx.x < 4)
+            part_acc[((size_t)level * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = 0.0;
+        return;
+    }
     int64_t begin, end;
-    chunk_of(C, begin, end);
+    chunk_of(C, G, begin, end);
 
     __shared__ int s_warp[32];
     __shared__ int s_total;
@@ -350,7 +476,7 @@ __device__ __forceinline__ void compact_body(const Desc* __restrict__ desc,
                         (uint32_t)cell_coord(D, level, q, i, parents_prev, st);
         } else if (valid) {
             val.add(ms.x);
-            var.add(ms.y * ms.y / T);
+            var.add(ms.y * ms.y);  // divided by T once, in the final reduction
         }
         offset += s_total;
         __syncthreads();
@@ -365,7 +491,8 @@ __device__ __forceinline__ void compact_body(const Desc* __restrict__ desc,
 
 // Step (c): the compensated sum of every level's accepted partial sums, and
 // the result record.  One CTA.
-__device__ __forceinline__ void final_body(const State* __restrict__ st,
+__device__ __forceinline__ void final_body(const Desc* __restrict__ desc,
+                                           const State* __restrict__ st,
                                            const double* __restrict__ part_acc, int sel_grid,
                                            zmc_result* __restrict__ out) {
     const int levels = st->levels_run;
@@ -381,7 +508,7 @@ __device__ __forceinline__ void final_body(const State* __restrict__ st,
     var = block_csum(var);
     if (threadIdx.x == 0) {
         out->value = val.s + val.e;
-        out->std = sqrt(var.s + var.e);
+        out->std = sqrt((var.s + var.e) / desc->T);
         int64_t cells = 0;
         for (int L = 1; L <= ZMC_MAX_DEPTH; ++L) {
             const bool ran = L <= levels;
@@ -422,8 +549,9 @@ zmc_compact(const Desc* desc, const State* st, const double2* cell_stats,
     compact_body(desc, st, cell_stats, part_offset, parents_prev, parents_next, part_acc, level);
 }
 __global__ void __launch_bounds__(kSelThreads)
-zmc_final(const State* st, const double* part_acc, int sel_grid, zmc_result* out) {
-    final_body(st, part_acc, sel_grid, out);
+zmc_final(const Desc* desc, const State* st, const double* part_acc, int sel_grid,
+          zmc_result* out) {
+    final_body(desc, st, part_acc, sel_grid, out);
 }
 
 // A batch of integrations: row blockIdx.y of the grid works on items[y].
@@ -451,7 +579,7 @@ zmc_compact_batch(const Buffers* items, int level) {
 __global__ void __launch_bounds__(kSelThreads)
 zmc_final_batch(const Buffers* items, zmc_result* out) {
     const Buffers& b = items[blockIdx.y];
-    final_body(b.state, b.part_acc, kSelGrid, &out[blockIdx.y]);
+    final_body(b.desc, b.state, b.part_acc, kSelGrid, &out[blockIdx.y]);
 }
 
 // Philox words for bit-exact checks of the generator used by kernel (a).
@@ -538,7 +666,7 @@ cudaError_t launch_select(const Buffers& b, int level, const uint32_t* parents_p
 }
 
 cudaError_t launch_final(const Buffers& b, cudaStream_t s) {
-    zmc_final<<<1, kSelThreads, 0, s>>>(b.state, b.part_acc, kSelGrid, b.result);
+    zmc_final<<<1, kSelThreads, 0, s>>>(b.desc, b.state, b.part_acc, kSelGrid, b.result);
     return cudaGetLastError();
 }
 
