@@ -193,7 +193,7 @@ ZMC_API int zmc_launch_shape(zmc_handle h, int* threads, int* grid);
  *   [0] target_units          a level is cut into at least this many units
  *                             when its tiles allow, 1 .. 2^18
  *   [1] min_unit_groups       ... but no unit has fewer point groups (of 4
- *                             points in FP64, 5 in the FP32 modes), >= 1:
+ *                             points in FP64, 11 in the FP32 modes), >= 1:
  *                             "samples per thread" is 1/32 of a unit
  *   [2] lane_tile_groups      tiles of fewer groups always run one per lane
  *   [3] lane_tile_max_groups  tiles of fewer groups run one per lane on ...
@@ -209,6 +209,15 @@ ZMC_API int zmc_launch_shape(zmc_handle h, int* threads, int* grid);
  * least 2% faster, cached per (kernel, dimension, n, level size) for the
  * process and recorded in the results.  An explicit zmc_set_launch /
  * zmc_set_work_plan wins over the tuner.  Errors: ZMC_ERR_ARG.
+ *
+ * Persisted choices: with ZMC_TUNE_CACHE=<path> in the environment, every
+ * tuned shape and plan is also appended to that file (one JSON object per
+ * line, keyed by device name, SM count, compute capability, a hash of the
+ * library build, precision, integrand or a hash of the expression, and the
+ * problem's dimension -- plus n and level size for a plan), and a later
+ * process reads the file before timing anything.  Lines that do not parse or
+ * hold values a setter would reject are skipped; a file that cannot be read
+ * or written only disables the persistence.
  */
 #define ZMC_TUNE_SHAPE 1
 #define ZMC_TUNE_PLAN 2

@@ -7,6 +7,7 @@ host with the NVIDIA driver (and on hosts without one, for symbol checks).
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
 import shutil
 import subprocess
@@ -99,6 +100,20 @@ def _newest_input() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
+def _build_id(sources: list, checked: bool) -> str:
+    """64-bit hash of everything that goes into the library (sources,
+    headers, flags); the tuner's file cache keys its entries by it."""
+    h = hashlib.sha256()
+    files = sorted(set(sources) | {os.path.join(CSRC, f) for f in os.listdir(CSRC)}
+                   | {os.path.join(INCLUDE, "zmc.h")})
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    h.update(" ".join(ARCH + FLAGS + (["checked"] if checked else [])).encode())
+    return "0x%sULL" % h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
           checked: bool = False) -> str:
     """Compile every translation unit and link libzmc.so; returns its path.
@@ -116,6 +131,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
     extra = ["-Xptxas", "-v"] if ptxas_info else []
     if checked:
         extra = extra + ["-DZMC_CHECKED"]
+    extra = extra + ["-DZMC_BUILD_ID=" + _build_id(sources, checked)]
 
     def compile_one(src):
         obj = os.path.join(build_dir, os.path.splitext(os.path.basename(src))[0] + ".o")

@@ -1,6 +1,7 @@
 // The C ABI of include/zmc.h: handles, argument checks, device buffers, the
 // per-level launch sequence (captured once into a CUDA graph and replayed),
 // tracing, and the single host <-> device crossing of a run.
+#include <ctype.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <nvtx3/nvToolsExt.h>
@@ -361,13 +362,138 @@ const void* eval_kernel(const zmc_ctx* h) {
 // threads per CTA, and from the occupancy limit down to half of it CTAs per
 // SM.  Each is timed once on a truncated level 1 of the caller's own
 // problem (about 2^29 points), the fastest is kept per (kernel, dimension)
-// for the life of the process.  ZMC_TUNE=0 in the environment, or an
-// explicit zmc_set_launch(), skips it.
+// for the life of the process (and, with ZMC_TUNE_CACHE, in a file; see
+// below).  ZMC_TUNE=0 in the environment, or an explicit zmc_set_launch(),
+// skips it.
 struct Tuned {
     int threads, per_sm;
 };
 std::mutex g_tune_mu;
 std::map<std::pair<const void*, int>, Tuned> g_tuned;
+
+#ifndef ZMC_BUILD_ID
+#define ZMC_BUILD_ID 0ULL   // the build passes a hash of the library's sources
+#endif
+
+// ------------------------------------------------- persisted tuner cache
+// With ZMC_TUNE_CACHE=<path> in the environment the tuner's choices are also
+// kept in that file, one JSON object per line, appended as they are made, so
+// that a later process running the same build of the library on the same
+// kind of GPU skips the timing runs.  A line's key names the device (name,
+// SM count, compute capability), the build (a hash of the library's
+// sources), the kernel (precision mode and registry integrand, or a hash of
+// the expression) and the problem's shape.  Lines that do not parse, or whose
+// values a setter would reject, are ignored; a file that cannot be read or
+// written is not an error.  Without the variable nothing is read or written.
+bool plan_ok(const WorkPlan& w) {
+    return w.target_units >= 1 && w.target_units <= kTargetUnits && w.min_unit_groups >= 1 &&
+           w.lane_tile_groups >= 0 && w.lane_tile_max_groups >= 0 &&
+           w.lane_tile_min_tiles >= 1;
+}
+
+struct DiskCache {
+    std::string path;                          // the file loaded ("" before any)
+    std::map<std::string, Tuned> shapes;       // by shape_key
+    std::map<std::string, WorkPlan> plans;     // by plan_key
+    std::map<int, std::string> device_tags;    // by device ordinal
+};
+DiskCache g_disk;   // guarded by g_tune_mu
+
+const char* tune_cache_path() {
+    const char* p = getenv("ZMC_TUNE_CACHE");
+    return (p && *p) ? p : nullptr;
+}
+
+uint64_t fnv1a64(const std::string& text) {
+    uint64_t x = 0xcbf29ce484222325ULL;
+    for (unsigned char c : text) x = (x ^ c) * 0x100000001b3ULL;
+    return x;
+}
+
+// Caller holds g_tune_mu.
+const std::string& device_tag_locked(int device) {
+    auto it = g_disk.device_tags.find(device);
+    if (it != g_disk.device_tags.end()) return it->second;
+    std::string tag = "unknown";
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) {
+        std::string name = prop.name;
+        for (char& c : name)
+            if (!isalnum((unsigned char)c)) c = '_';
+        char buf[384];
+        snprintf(buf, sizeof buf, "%s/sm%d/cc%d.%d/build%016llx", name.c_str(),
+                 prop.multiProcessorCount, prop.major, prop.minor,
+                 (unsigned long long)ZMC_BUILD_ID);
+        tag = buf;
+    } else {
+        cudaGetLastError();
+    }
+    return g_disk.device_tags[device] = tag;
+}
+
+std::string kernel_tag(const zmc_ctx* h) {
+    char buf[96];
+    if (h->integrand == kExpression)
+        snprintf(buf, sizeof buf, "expr/m%d/p%zu/%016llx", h->mode, h->params.size(),
+                 (unsigned long long)fnv1a64(h->expr));
+    else
+        snprintf(buf, sizeof buf, "reg/m%d/f%d", h->mode, h->integrand);
+    return buf;
+}
+
+std::string shape_key(const std::string& dev, const std::string& ker, int d) {
+    return dev + " " + ker + " d" + std::to_string(d);
+}
+std::string plan_key(const std::string& dev, const std::string& ker, int d, long long n,
+                     long long tiles) {
+    return shape_key(dev, ker, d) + " n" + std::to_string(n) + " t" + std::to_string(tiles);
+}
+
+static_assert(ZMC_PLAN_FIELDS == 5, "the cache's plan lines hold five fields");
+constexpr const char* kShapeLine =
+    "{\"kind\": \"shape\", \"device\": \"%s\", \"kernel\": \"%s\", \"d\": %d, "
+    "\"threads\": %d, \"per_sm\": %d}\n";
+constexpr const char* kPlanLine =
+    "{\"kind\": \"plan\", \"device\": \"%s\", \"kernel\": \"%s\", \"d\": %d, "
+    "\"n\": %lld, \"tiles\": %lld, \"plan\": [%lld, %lld, %lld, %lld, %lld]}\n";
+
+// Caller holds g_tune_mu.  Reads the file once per path.
+void disk_load_locked(const char* path) {
+    if (g_disk.path == path) return;
+    g_disk.path = path;
+    g_disk.shapes.clear();
+    g_disk.plans.clear();
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    char line[1024];
+    while (fgets(line, sizeof line, f)) {
+        char dev[320], ker[96];
+        int d = 0, threads = 0, per_sm = 0;
+        long long n = 0, tiles = 0, p[ZMC_PLAN_FIELDS];
+        if (sscanf(line,
+                   " {\"kind\": \"shape\", \"device\": \"%319[^\"]\", \"kernel\": "
+                   "\"%95[^\"]\", \"d\": %d, \"threads\": %d, \"per_sm\": %d}",
+                   dev, ker, &d, &threads, &per_sm) == 5) {
+            if ((threads == 64 || threads == 128 || threads == 256) && per_sm >= 1)
+                g_disk.shapes[shape_key(dev, ker, d)] = Tuned{threads, per_sm};
+        } else if (sscanf(line,
+                          " {\"kind\": \"plan\", \"device\": \"%319[^\"]\", \"kernel\": "
+                          "\"%95[^\"]\", \"d\": %d, \"n\": %lld, \"tiles\": %lld, "
+                          "\"plan\": [%lld, %lld, %lld, %lld, %lld]}",
+                          dev, ker, &d, &n, &tiles, &p[0], &p[1], &p[2], &p[3], &p[4]) == 10) {
+            const WorkPlan w{p[0], p[1], p[2], p[3], p[4]};
+            if (plan_ok(w)) g_disk.plans[plan_key(dev, ker, d, n, tiles)] = w;
+        }
+    }
+    fclose(f);
+}
+
+void disk_append(const char* path, const char* line) {
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fputs(line, f);
+    fclose(f);
+}
 
 int occupancy(const void* kernel, int threads) {
     int per_sm = 0;
@@ -409,10 +535,23 @@ Tuned tuned_shape(zmc_ctx* h, cudaStream_t s) {
     const char* env = getenv("ZMC_TUNE");
     if ((env && strcmp(env, "0") == 0) || !(h->tuning & ZMC_TUNE_SHAPE)) return default_shape(h);
     const std::pair<const void*, int> key(eval_kernel(h), h->dim);
+    const char* cache = tune_cache_path();
+    std::string dev, ker = kernel_tag(h);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) return it->second;
+        if (cache) {
+            dev = device_tag_locked(h->device);
+            disk_load_locked(cache);
+            auto jt = g_disk.shapes.find(shape_key(dev, ker, h->dim));
+            if (jt != g_disk.shapes.end()) {
+                Tuned t = jt->second;
+                t.per_sm = std::min(t.per_sm, occupancy(eval_kernel(h), t.threads));
+                g_tuned[key] = t;
+                return t;
+            }
+        }
     }
     // Nothing may be timed while the caller's stream is being captured: the
     // default shape then (not cached, so a later uncaptured run tunes).
@@ -463,6 +602,13 @@ Tuned tuned_shape(zmc_ctx* h, cudaStream_t s) {
     cudaGetLastError();
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tuned[key] = best;
+    if (cache) {
+        g_disk.shapes[shape_key(dev, ker, h->dim)] = best;
+        char line[640];
+        snprintf(line, sizeof line, kShapeLine, dev.c_str(), ker.c_str(), h->dim, best.threads,
+                 best.per_sm);
+        disk_append(cache, line);
+    }
     return best;
 }
 
@@ -505,10 +651,19 @@ WorkPlan tuned_plan(zmc_ctx* h, Tuned shape, cudaStream_t s) {
     const int64_t K = ipow_sat(h->k, h->dim, INT64_MAX);
     if (K > kPlanTuneMaxPoints / (h->n * (int64_t)h->T)) return kDefaultPlan;
     const PlanKey key{eval_kernel(h), h->dim, h->n, K * h->T};
+    const char* cache = tune_cache_path();
+    std::string dkey;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tuned_plan.find(key);
         if (it != g_tuned_plan.end()) return it->second;
+        if (cache) {
+            dkey = plan_key(device_tag_locked(h->device), kernel_tag(h), h->dim, h->n,
+                            K * h->T);
+            disk_load_locked(cache);
+            auto jt = g_disk.plans.find(dkey);
+            if (jt != g_disk.plans.end()) return g_tuned_plan[key] = jt->second;
+        }
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
@@ -553,6 +708,16 @@ WorkPlan tuned_plan(zmc_ctx* h, Tuned shape, cudaStream_t s) {
     if (ok) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tuned_plan[key] = best;
+        if (cache) {
+            g_disk.plans[dkey] = best;
+            char line[768];
+            snprintf(line, sizeof line, kPlanLine, device_tag_locked(h->device).c_str(),
+                     kernel_tag(h).c_str(), h->dim, (long long)h->n, (long long)(K * h->T),
+                     (long long)best.target_units, (long long)best.min_unit_groups,
+                     (long long)best.lane_tile_groups, (long long)best.lane_tile_max_groups,
+                     (long long)best.lane_tile_min_tiles);
+            disk_append(cache, line);
+        }
     }
     return best;
 }
@@ -969,8 +1134,7 @@ ZMC_API int zmc_set_work_plan(zmc_handle h, const int64_t* plan) {
     } else {
         WorkPlan w;
         memcpy(&w, plan, sizeof w);
-        if (w.target_units < 1 || w.target_units > kTargetUnits || w.min_unit_groups < 1 ||
-            w.lane_tile_groups < 0 || w.lane_tile_max_groups < 0 || w.lane_tile_min_tiles < 1)
+        if (!plan_ok(w))
             return fail(h, ZMC_ERR_ARG,
                         "work plan: need 1 <= target_units <= 2^18, min_unit_groups >= 1, "
                         "lane_tile_groups >= 0, lane_tile_max_groups >= 0, "

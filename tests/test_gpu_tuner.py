@@ -97,3 +97,86 @@ def test_tuned_plan_is_not_slower_and_reproduces(zmc, w):
     assert (r.value, r.std, r.flagged_per_level) == (r_tuned.value, r_tuned.std,
                                                      r_tuned.flagged_per_level)
     assert r.work_plan == r_tuned.work_plan
+
+
+# ------------------------------------------------------------------ the file
+# ZMC_TUNE_CACHE: a first process writes its tuned choices to the file; a
+# second process with the same library and GPU takes them from the file
+# (edited here, so that taking them shows) and times nothing, skipping lines
+# that do not parse or hold values a setter would reject.
+CACHE_CHILD = r"""
+import json, sys
+sys.path.insert(0, sys.argv[1])
+from paper_1902_07916_gb300 import zmc
+out = {}
+for name, dim, k, n, trials, prec, tuning in json.loads(sys.argv[2]):
+    with zmc.Integrator(dim, [0.0] * dim, [1.0] * dim, k, n, trials, 1, 1.0, 5, "sin_sum", [],
+                        precision=zmc.PRECISIONS[prec]) as it:
+        zmc.zmc_set_tuning(it.h, tuning)
+        r = it.integrate()
+        out[name] = [list(zmc.zmc_launch_shape(it.h)), list(r.work_plan)]
+print(json.dumps(out))
+"""
+
+
+def cache_child(zmc, path, cases):
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ)
+    env.pop("ZMC_TUNE", None)
+    env["ZMC_TUNE_CACHE"] = path
+    env["ZMC_LIBRARY"] = zmc.LIB_PATH
+    r = subprocess.run([sys.executable, "-c", CACHE_CHILD, root, json.dumps(cases)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def test_tuned_choices_persist_in_the_cache_file(zmc, tmp_path):
+    import json
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    # a shape-only handle (FP32, d = 4) and a shape + plan handle (FP64,
+    # d = 3, level 1 of 2^26 points, inside the plan tuner's 2^31 limit)
+    cases = [["shape", 4, 6, 1000, 5, "fp32_fp64acc", zmc.ZMC_TUNE_SHAPE],
+             ["plan", 3, 16, 2048, 8, "fp64", zmc.ZMC_TUNE_SHAPE | zmc.ZMC_TUNE_PLAN]]
+    path = str(tmp_path / "tune.jsonl")
+    first = cache_child(zmc, path, cases)
+    lines = [json.loads(x) for x in open(path).read().splitlines()]
+    shapes = {(x["kernel"], x["d"]) for x in lines if x["kind"] == "shape"}
+    plans = [x for x in lines if x["kind"] == "plan"]
+    assert len(lines) == 3 and len(plans) == 1, lines
+    assert any(k.startswith("reg/m1/") and d == 4 for k, d in shapes), shapes
+    assert any(k.startswith("reg/m0/") and d == 3 for k, d in shapes), shapes
+    assert plans[0]["d"] == 3 and plans[0]["n"] == 2048 and plans[0]["tiles"] == 16 ** 3 * 8
+    assert plans[0]["plan"] == first["plan"][1]
+    for x in lines:
+        assert x["device"] == lines[0]["device"] and "/sm%d/" % sms in x["device"]
+
+    # edit the choices: 128 threads and one CTA per SM, another valid plan;
+    # add lines the reader must skip
+    other_plan = [1 << 17, 256, 64, 1024, 1 << 15]
+    edited = []
+    for x in lines:
+        if x["kind"] == "shape":
+            x.update(threads=128, per_sm=1)
+            edited.append(json.dumps(dict(x, threads=100)))
+        else:
+            x["plan"] = other_plan
+        edited.append(json.dumps(x))
+    edited.insert(0, "not a cache line")
+    edited.append('{"kind": "plan", "device": "x", "kernel": "y", "d": 1, "n": 2, '
+                  '"tiles": 3, "plan": [0, 0, 0, 0, 0]}')
+    text = "\n".join(edited) + "\n"
+    with open(path, "w") as fh:
+        fh.write(text)
+    second = cache_child(zmc, path, cases)
+    for name in ("shape", "plan"):
+        assert second[name][0] == [128, sms], (name, second[name])
+    assert second["plan"][1] == other_plan
+    assert second["shape"][1] == DEFAULT_PLAN
+    # everything came from the file: nothing was timed, nothing appended
+    assert open(path).read() == text
