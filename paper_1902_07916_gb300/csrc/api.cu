@@ -283,7 +283,7 @@ int ensure_device(zmc_ctx* h) {
         {(void**)&b.part_count, sizeof(int64_t) * kSelGrid},
         {(void**)&b.part_offset, sizeof(int64_t) * kSelGrid},
         {(void**)&b.part_margin, sizeof(double) * kSelGrid},
-        {(void**)&b.part_acc, sizeof(double) * 4 * kSelGrid * (ZMC_MAX_DEPTH + 1)},
+        {(void**)&b.part_acc, sizeof(double) * kPartAccDoubles},
         {(void**)&b.result, sizeof(zmc_result)},
     };
     for (const Req& r : reqs) {
@@ -293,7 +293,7 @@ int ensure_device(zmc_ctx* h) {
             return cuda_fail(h, e, "cudaMalloc of the level buffers");
         }
     }
-    cudaError_t e = cudaMemset(b.part_acc, 0, sizeof(double) * 4 * kSelGrid * (ZMC_MAX_DEPTH + 1));
+    cudaError_t e = cudaMemset(b.part_acc, 0, sizeof(double) * kPartAccDoubles);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_desc, sizeof(Desc));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_result, sizeof(zmc_result));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);

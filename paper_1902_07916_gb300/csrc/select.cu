@@ -139,6 +139,50 @@ __device__ __forceinline__ double div_rn(double a, double b, double rb) {
     return fma(fma(-q0, b, a), rb, q0);
 }
 
+// Mean and sum of squared deviations of one cell's trial estimates
+// I_t = V S1_t / n, S1_t = row[t * chunks].x.  With TMAX > 0 (and T <= TMAX)
+// the estimates stay in registers between the two passes; with TMAX = 0
+// the second pass computes them again (the same bits).
+constexpr int kStatsRegTrials = 16;
+template <int TMAX>
+__device__ __forceinline__ void cell_moments(const double2* row, int64_t chunks, int T, double V,
+                                             double n, double rn, double Td, double rT,
+                                             double& mean, double& ss, bool& finite) {
+    double s = 0.0;
+    ss = 0.0;
+    if constexpr (TMAX > 0) {
+        double x[TMAX];
+#pragma unroll
+        for (int t = 0; t < TMAX; ++t) {
+            if (t < T) {
+                const double S1 = row[t * chunks].x;
+                finite = finite && isfinite(S1);
+                x[t] = div_rn(V * S1, n, rn);
+                s += x[t];
+            }
+        }
+        mean = div_rn(s, Td, rT);
+#pragma unroll
+        for (int t = 0; t < TMAX; ++t) {
+            if (t < T) {
+                const double e = x[t] - mean;
+                ss = fma(e, e, ss);
+            }
+        }
+    } else {
+        for (int t = 0; t < T; ++t) {
+            const double S1 = row[t * chunks].x;
+            finite = finite && isfinite(S1);
+            s += div_rn(V * S1, n, rn);
+        }
+        mean = div_rn(s, Td, rT);
+        for (int t = 0; t < T; ++t) {
+            const double e = div_rn(V * row[t * chunks].x, n, rn) - mean;
+            ss = fma(e, e, ss);
+        }
+    }
+}
+
 // How many CTAs of the (fixed) grid take part in a selection step over
 // `work` units, at least `per_cta` units each: CTAs beyond that would only
 // add block reductions.  A function of the level's size only, so the
@@ -205,7 +249,8 @@ __device__ __forceinline__ void init_state_body(const Desc* __restrict__ desc, S
 // at two operations per SM per clock on GB300, so the kernel keeps FP64
 // divisions out of its loops: I_{c,t} and the mean are correctly rounded
 // quotients from precomputed reciprocals (div_rn; the same bits as a
-// division, so a cell whose trials agree has spread 0 exactly), and the
+// division, so a cell whose trials agree has spread 0 exactly), up to 16
+// trials' estimates stay in registers between the two passes, and the
 // moments of the spreads are taken in two passes with plain sums -- per CTA
 // over its cells, then over the CTAs' (count, mean, M2) -- instead of
 // pairwise merges.
@@ -247,18 +292,11 @@ __device__ __forceinline__ void cell_stats_body(const Desc* __restrict__ desc, S
         }
         // Only S1 enters the method; S2 (a within-cell diagnostic) may
         // overflow in the FP32 modes when |f| exceeds ~1.8e19.
-        double s = 0.0;
-        for (int t = 0; t < T; ++t) {
-            const double S1 = row[t * chunks].x;
-            finite = finite && isfinite(S1);
-            s += div_rn(V * S1, n, rn);
-        }
-        const double mean = div_rn(s, Td, rT);
-        double ss = 0.0;
-        for (int t = 0; t < T; ++t) {
-            const double e = div_rn(V * row[t * chunks].x, n, rn) - mean;
-            ss = fma(e, e, ss);
-        }
+        double mean, ss;
+        if (T <= kStatsRegTrials)
+            cell_moments<kStatsRegTrials>(row, chunks, T, V, n, rn, Td, rT, mean, ss, finite);
+        else
+            cell_moments<0>(row, chunks, T, V, n, rn, Td, rT, mean, ss, finite);
         const double spread = sqrt(ss * inv_T1);
         cell_stats[q] = make_double2(mean, spread);
         tsum += spread;
@@ -425,8 +463,7 @@ __device__ __forceinline__ void flag_count_body(const Desc* __restrict__ desc, S
 // the next level's parent list (the children themselves are implicit:
 // child slot r*K + digit); add the accepted cells' mean and spread^2 / T to
 // this level's compensated partial sums.
-__device__ __forceinline__ void compact_body(const Desc* __restrict__ desc,
-                                             const State* __restrict__ st,
+__device__ __forceinline__ void compact_body(const Desc* __restrict__ desc, State* st,
                                              const double2* __restrict__ cell_stats,
                                              const int64_t* __restrict__ part_offset,
                                              const uint32_t* __restrict__ parents_prev,
@@ -439,12 +476,7 @@ __device__ __forceinline__ void compact_body(const Desc* __restrict__ desc,
     const double theta = st->theta[level];
     const int d = D.d;
     const int G = active_ctas(C, kCellsPerCta);
-    if ((int)blockIdx.x >= G) {
-        // the final reduction reads every CTA's slot
-        if (threadIdx.x < 4)
-            part_acc[((size_t)level * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = 0.0;
-        return;
-    }
+    if ((int)blockIdx.x >= G) return;
     int64_t begin, end;
     chunk_of(C, G, begin, end);
 
@@ -484,8 +516,24 @@ __device__ __forceinline__ void compact_body(const Desc* __restrict__ desc,
     val = block_csum(val);
     var = block_csum(var);
     if (threadIdx.x == 0) {
-        double* p = part_acc + ((size_t)level * gridDim.x + blockIdx.x) * 4;
+        double* p = part_acc + (size_t)blockIdx.x * 4;
         p[0] = val.s; p[1] = val.e; p[2] = var.s; p[3] = var.e;
+    }
+    if (!last_to_arrive(&st->ticket[2], G)) return;
+
+    // the level's slot: the CTAs' compensated partials added in CTA order
+    CSum lv{0.0, 0.0}, lw{0.0, 0.0};
+    for (int b = threadIdx.x; b < G; b += blockDim.x) {
+        const double* p = part_acc + (size_t)b * 4;
+        lv.add(CSum{__ldcg(p), __ldcg(p + 1)});
+        lw.add(CSum{__ldcg(p + 2), __ldcg(p + 3)});
+    }
+    lv = block_csum(lv);
+    lw = block_csum(lw);
+    if (threadIdx.x == 0) {
+        double* p = part_acc + ((size_t)kSelGrid + level) * 4;
+        p[0] = lv.s; p[1] = lv.e; p[2] = lw.s; p[3] = lw.e;
+        st->ticket[2] = 0u;
     }
 }
 
@@ -493,16 +541,14 @@ __device__ __forceinline__ void compact_body(const Desc* __restrict__ desc,
 // the result record.  One CTA.
 __device__ __forceinline__ void final_body(const Desc* __restrict__ desc,
                                            const State* __restrict__ st,
-                                           const double* __restrict__ part_acc, int sel_grid,
+                                           const double* __restrict__ part_acc,
                                            zmc_result* __restrict__ out) {
     const int levels = st->levels_run;
     CSum val{0.0, 0.0}, var{0.0, 0.0};
-    for (int L = 1; L <= levels; ++L) {
-        for (int b = threadIdx.x; b < sel_grid; b += blockDim.x) {
-            const double* p = part_acc + ((size_t)L * sel_grid + b) * 4;
-            val.add(CSum{p[0], p[1]});
-            var.add(CSum{p[2], p[3]});
-        }
+    for (int L = 1 + threadIdx.x; L <= levels; L += blockDim.x) {
+        const double* p = part_acc + ((size_t)kSelGrid + L) * 4;
+        val.add(CSum{p[0], p[1]});
+        var.add(CSum{p[2], p[3]});
     }
     val = block_csum(val);
     var = block_csum(var);
@@ -543,15 +589,14 @@ zmc_flag_count(const Desc* desc, State* st, const double2* cell_stats, int64_t* 
     flag_count_body(desc, st, cell_stats, part_count, part_offset, part_margin, level);
 }
 __global__ void __launch_bounds__(kSelThreads)
-zmc_compact(const Desc* desc, const State* st, const double2* cell_stats,
+zmc_compact(const Desc* desc, State* st, const double2* cell_stats,
             const int64_t* part_offset, const uint32_t* parents_prev, uint32_t* parents_next,
             double* part_acc, int level) {
     compact_body(desc, st, cell_stats, part_offset, parents_prev, parents_next, part_acc, level);
 }
 __global__ void __launch_bounds__(kSelThreads)
-zmc_final(const Desc* desc, const State* st, const double* part_acc, int sel_grid,
-          zmc_result* out) {
-    final_body(desc, st, part_acc, sel_grid, out);
+zmc_final(const Desc* desc, const State* st, const double* part_acc, zmc_result* out) {
+    final_body(desc, st, part_acc, out);
 }
 
 // A batch of integrations: row blockIdx.y of the grid works on items[y].
@@ -579,7 +624,7 @@ zmc_compact_batch(const Buffers* items, int level) {
 __global__ void __launch_bounds__(kSelThreads)
 zmc_final_batch(const Buffers* items, zmc_result* out) {
     const Buffers& b = items[blockIdx.y];
-    final_body(b.desc, b.state, b.part_acc, kSelGrid, &out[blockIdx.y]);
+    final_body(b.desc, b.state, b.part_acc, &out[blockIdx.y]);
 }
 
 // Philox words for bit-exact checks of the generator used by kernel (a).
@@ -666,7 +711,7 @@ cudaError_t launch_select(const Buffers& b, int level, const uint32_t* parents_p
 }
 
 cudaError_t launch_final(const Buffers& b, cudaStream_t s) {
-    zmc_final<<<1, kSelThreads, 0, s>>>(b.desc, b.state, b.part_acc, kSelGrid, b.result);
+    zmc_final<<<1, kSelThreads, 0, s>>>(b.desc, b.state, b.part_acc, b.result);
     return cudaGetLastError();
 }
 

@@ -22,14 +22,21 @@ struct Buffers {
     int64_t* part_count;  // [kSelGrid]
     int64_t* part_offset; // [kSelGrid]
     double* part_margin;  // [kSelGrid]
-    double* part_acc;     // [(ZMC_MAX_DEPTH + 1) * kSelGrid * 4]
+    double* part_acc;     // [kPartAccDoubles] see below
     zmc_result* result;
 };
 
 // Selection kernels run on a fixed grid so that their reduction order, and
 // hence every bit of the result, does not depend on the GPU's SM count.
-constexpr int kSelGrid = 256;
+// 608 = 4 x 152: on GB300 a full level occupies every SM evenly (four CTAs
+// of 256 threads each); levels of less work use fewer of them (active_ctas).
+constexpr int kSelGrid = 608;
 constexpr int kSelThreads = 256;
+// part_acc: the compaction CTAs' compensated (value, variance) partials of
+// the level being compacted, kSelGrid x 4, then one slot of 4 per level
+// (0 .. ZMC_MAX_DEPTH) written by the level's last CTA and read by the
+// final reduction.
+constexpr size_t kPartAccDoubles = 4 * ((size_t)kSelGrid + ZMC_MAX_DEPTH + 1);
 
 // Launch shape of the sampling kernel.
 struct EvalShape {
