@@ -28,9 +28,11 @@ struct Buffers {
 
 // Selection kernels run on a fixed grid so that their reduction order, and
 // hence every bit of the result, does not depend on the GPU's SM count.
-// 608 = 4 x 152: on GB300 a full level occupies every SM evenly (four CTAs
-// of 256 threads each); levels of less work use fewer of them (active_ctas).
-constexpr int kSelGrid = 608;
+// Levels of little work use fewer of the grid's CTAs (active_ctas).  256
+// measured best overall: 608 (four CTAs on each of GB300's 152 SMs) saved
+// 0.04 ms per 6-D sine step but cost 3 ms per 512-integral batch, whose
+// 256 x 512 grid is mostly CTAs that exit at once.
+constexpr int kSelGrid = 256;
 constexpr int kSelThreads = 256;
 // part_acc: the compaction CTAs' compensated (value, variance) partials of
 // the level being compacted, kSelGrid x 4, then one slot of 4 per level
