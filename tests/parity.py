@@ -46,6 +46,20 @@ def sums_tolerance(ref_sums: np.ndarray, n: int, rtol: float) -> np.ndarray:
     return tol
 
 
+def spread_tolerance(ref_sums: np.ndarray, volume: float, n: int, rtol: float) -> np.ndarray:
+    """Tolerance per cell of its sample spread s (ddof 1 over the T trial
+    estimates I_t = V S1_t / n, Sec. 2.1) induced by the allowed error of the
+    trials' sums: s moves by at most sqrt(T / (T - 1)) times the largest
+    change of an I_t, and each I_t carries a few ulps of its own rounding.
+    Relative to s itself this is large where the trials agree closely (s
+    then is a difference of nearly equal numbers)."""
+    T = ref_sums.shape[1]
+    tol1 = sums_tolerance(ref_sums, n, rtol)[..., 0]
+    est = volume * np.abs(ref_sums[..., 0]) / n
+    return math.sqrt(T / (T - 1)) * (volume / n * tol1.max(axis=1)
+                                      + 4 * np.finfo(np.float64).eps * est.max(axis=1))
+
+
 def compare_fp64(w, res, levels, ref, check_sums=True):
     """Exact decisions and FP64 tolerances, level by level."""
     assert res.levels_run == ref.levels_run, (res.levels_run, ref.levels_run)
@@ -58,7 +72,14 @@ def compare_fp64(w, res, levels, ref, check_sums=True):
                 L, float(err.max()))
         np.testing.assert_allclose(g["cell_stats"][:, 0], r.mean, rtol=1e-11,
                                    atol=1e-11 * np.abs(r.mean).max() + 1e-300)
-        np.testing.assert_allclose(g["cell_stats"][:, 1], r.spread, rtol=1e-10, atol=1e-300)
+        volume = math.prod((b - a) / w.k ** L for a, b in zip(w.lo, w.hi))
+        spread_err = np.abs(g["cell_stats"][:, 1] - r.spread)
+        bound = np.maximum(1e-10 * r.spread, spread_tolerance(r.sums, volume, w.n,
+                                                              FP64_SUM_RTOL)) + 1e-300
+        assert np.all(spread_err <= bound), (L, float((spread_err / bound).max()))
+        # a cell whose trial sums are identical has spread 0 exactly
+        same = np.all(g["sums"][:, :, 0] == g["sums"][:, :1, 0], axis=1)
+        assert np.all(g["cell_stats"][same, 1] == 0.0), L
         assert math.isclose(g["theta"], r.theta, rel_tol=1e-10, abs_tol=1e-300), L
         if r.min_margin < TIE_MARGIN:
             raise AssertionError("tie (unpinned): level %d margin %g" % (L, r.min_margin))

@@ -93,6 +93,15 @@ FP64_CASES = [
     W("gaussnorm3", "gauss_norm", 3, -1.0, 1.0, 4, 64, 4, 3, 1.0, 8, [0.2]),
     W("osc3", "genz_osc", 3, 0.0, 1.0, 3, 50, 5, 3, 0.8, 6, [0.3, 4.0, 8.0, 2.0]),
     W("sin6_tiles", "sin_sum", 6, 0.0, 10.0, 4, 256, 10, 2, 1.5, 2),
+    # Level sizes around the selection kernels' CTA counts (one CTA per 1024
+    # cells for flag and compaction, per 4096 (cell, trial) sums for the
+    # statistics, at most the 256-CTA grid): exactly one CTA, two CTAs with
+    # an uneven split, twelve, and the capped grid with a short last chunk.
+    W("sel_1024", "genz_osc", 2, 0.0, 1.0, 32, 40, 4, 2, 1.0, 21, [0.3, 4.0, 8.0]),
+    W("sel_1089", "genz_osc", 2, 0.0, 1.0, 33, 40, 4, 2, 1.0, 22, [0.3, 4.0, 8.0]),
+    W("sel_12167", "genz_gauss", 3, 0.0, 1.0, 23, 24, 4, 1, 1.5, 23,
+      [6.0, 3.0, 5.0, 0.4, 0.7, 0.5]),
+    W("sel_270400", "genz_corner", 2, 0.0, 1.0, 520, 8, 2, 1, 1.0, 24, [3.0, 5.0]),
 ]
 
 
