@@ -131,11 +131,13 @@ __device__ bool last_to_arrive(uint32_t* ticket) { return last_to_arrive(ticket,
 // exact in an FMA, and one correction step q0 + (a - q0 b) rb rounds to the
 // correctly rounded quotient (Markstein's theorem on division with a
 // correctly rounded reciprocal, IBM J. Res. Dev. 34(1), 1990).  Zero, tiny
-// (remainder near the subnormal range) and non-finite quotients take the
-// plain division.
+// (|q0| < 2^-960: the remainder near the subnormal range) and non-finite
+// quotients take the plain division; the test reads q0's exponent field
+// with integer operations, leaving the FP64 pipe to the arithmetic.
 __device__ __forceinline__ double div_rn(double a, double b, double rb) {
     const double q0 = a * rb;
-    if (!(fabs(q0) >= 0x1p-960 && fabs(q0) <= DBL_MAX)) return a / b;
+    const unsigned ex = (unsigned)((unsigned long long)__double_as_longlong(q0) >> 52) & 0x7FFu;
+    if (ex < 1023u - 960u || ex == 0x7FFu) return a / b;
     return fma(fma(-q0, b, a), rb, q0);
 }
 
