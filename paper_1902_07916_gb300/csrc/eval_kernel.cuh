@@ -46,10 +46,17 @@ namespace zmc {
 
 constexpr int kEvalMaxThreads = 256;
 constexpr int kEvalMaxWarps = kEvalMaxThreads / 32;
-// CTAs of kEvalMaxThreads per SM the register allocation must allow: caps
-// registers at 64 (FP32 modes) and 85 (FP64, whose values take two).
+// CTAs of kEvalMaxThreads per SM the register allocation must allow: 3
+// caps registers at 85 (80 used).  The FP32 sine kernels take 2 (up to 128
+// registers, no spills, 16 warps per SM): measured 0.6-1.0% faster on the
+// sine workloads, while the corner-peak and Gaussian kernels lost 0.3-0.95%
+// that way and keep 3.  Expression kernels use the mode's value.
 template <int MODE>
 constexpr int eval_min_blocks() { return 3; }
+template <int MODE, int FN>
+constexpr int eval_min_blocks_fn() {
+    return (MODE != ZMC_FP64 && FN == kSinSum) ? 2 : eval_min_blocks<MODE>();
+}
 // The dimension loop of a point group (group_values) is unrolled 8-way,
 // which covers d <= 8 completely; for d = 9..16 the FP32 modes unroll it
 // completely, since the remainder iteration of an 8-way unroll cost 2-4%.
@@ -565,7 +572,7 @@ __device__ __forceinline__ void lane_tile_unit(
 
 // One kernel per dimension DIM: each holds only the sample loop its d needs.
 template <int MODE, int FN, int DIM>
-__global__ void __launch_bounds__(kEvalMaxThreads, eval_min_blocks<MODE>())
+__global__ void __launch_bounds__(kEvalMaxThreads, eval_min_blocks_fn<MODE, FN>())
 zmc_eval_reduce(const Desc* __restrict__ desc, State* st,
                 const uint32_t* __restrict__ parents, double2* __restrict__ partial,
                 int level, const PhiloxKeys keys) {
