@@ -17,12 +17,19 @@ namespace zmc {
 // FP32 modes one fewer than the single kernel: an integral's Philox round
 // keys are loaded into registers per unit (the single kernel takes them from
 // the constant bank as kernel parameters).
-template <int MODE>
-constexpr int batch_min_blocks() { return MODE == ZMC_FP64 ? eval_min_blocks<MODE>() : 3; }
+// FP32 kernels keep 80 registers (3 CTAs per SM) except the oscillatory
+// family's, which, like the single kernel's, runs faster at up to 128 (2 CTAs
+// per SM: -1.2% time on the 512-integral batch's oscillatory group); the
+// other families measured slower there (they spill more as the compiler
+// unrolls further).
+template <int MODE, int FN = -1>
+constexpr int batch_min_blocks() {
+    return MODE == ZMC_FP64 ? eval_min_blocks<MODE>() : (FN == kGenzOsc ? 2 : 3);
+}
 static_assert(kBatchThreads == kEvalMaxThreads, "shared slices are sized for kEvalMaxThreads");
 
 template <int MODE, int FN, bool HI>
-__global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<MODE>())
+__global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<MODE, FN>())
 zmc_batch_eval(const BatchEval* __restrict__ items, int count, int level,
                const int64_t* __restrict__ offsets, unsigned long long* head) {
     using R = typename ModeTraits<MODE>::R;

@@ -47,15 +47,17 @@ namespace zmc {
 constexpr int kEvalMaxThreads = 256;
 constexpr int kEvalMaxWarps = kEvalMaxThreads / 32;
 // CTAs of kEvalMaxThreads per SM the register allocation must allow: 3
-// caps registers at 85 (80 used).  The FP32 sine kernels take 2 (up to 128
+// caps registers at 85 (80 used).  The FP32 kernels of the sine of a sum and
+// of the oscillatory Genz family (a cosine of a linear sum) take 2 (up to 128
 // registers, no spills, 16 warps per SM): measured 0.6-1.0% faster on the
-// sine workloads, while the corner-peak and Gaussian kernels lost 0.3-0.95%
-// that way and keep 3.  Expression kernels use the mode's value.
+// sine workloads and up to 1.7% on the oscillatory ones, while the
+// corner-peak and Gaussian kernels lost 0.3-0.95% that way and keep 3.
+// Expression kernels use the mode's value.
 template <int MODE>
 constexpr int eval_min_blocks() { return 3; }
 template <int MODE, int FN>
 constexpr int eval_min_blocks_fn() {
-    return (MODE != ZMC_FP64 && FN == kSinSum) ? 2 : eval_min_blocks<MODE>();
+    return (MODE != ZMC_FP64 && (FN == kSinSum || FN == kGenzOsc)) ? 2 : eval_min_blocks<MODE>();
 }
 // The dimension loop of a point group (group_values) is unrolled 8-way,
 // which covers d <= 8 completely; for d = 9..16 the FP32 modes unroll it
