@@ -248,8 +248,8 @@ def algorithmic_bytes_per_launch(cells_per_level, n, trials, fp64):
 # kernel's sources it was taken on (profiles/zmc_eval_reduce_sin6d_traffic.md).
 TRAFFIC_CAPTURE = {
     "workload": "sin6d", "fp64": False,
-    "bytes_per_launch": (89088 + 0 + 10514432 + 180695552) / 2,
-    "sources_sha256": "71f47378755eecdde9e9926ce686b304a9474b48db067a9ab0ab3104b32e1aa9",
+    "bytes_per_launch": (430592 + 0 + 11683328 + 184357376) / 2,
+    "sources_sha256": "4dcd4bb21b36d2aedb6ef6c1d363548912d4d96195e5b44cbd8e3eb1cc3fb0cd",
 }
 KERNEL_SOURCES = ["eval_kernel.cuh", "zmc_device.cuh", "zmc_layout.h"]
 
