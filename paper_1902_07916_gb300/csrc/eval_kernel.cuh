@@ -428,6 +428,30 @@ struct LaneCoef {
     }
 };
 
+// FP64 sine of a sum with one width in every dimension (a cube domain): the
+// argument start + sum_i alpha (1 + w_i 2^-32) is (start + alpha d) +
+// (alpha 2^-32) S with S = sum_i w_i, an exact 64-bit integer sum of the
+// Philox words (< 2^36), so a point needs one FP64 add (S to double through
+// its bits) and one FMA instead of d FMAs.  GB300 runs FP64 at two
+// operations per SM per clock and the integer ALU is idle in this mode.
+// `on` is decided per unit from the fold coefficients' bits.
+struct EqFold {
+    bool on;
+    double al32, c0;
+};
+template <int MODE, int FN>
+__device__ __forceinline__ EqFold eq_fold(const typename ModeTraits<MODE>::R2* ab, int nd,
+                                          typename ModeTraits<MODE>::R start) {
+    EqFold e{false, 0.0, 0.0};
+    if constexpr (MODE == ZMC_FP64 && FN == kSinSum) {
+        const long long a0 = __double_as_longlong(ab[0].x);
+        bool same = true;
+        for (int i = 1; i < nd; ++i) same = same && __double_as_longlong(ab[i].x) == a0;
+        if (same) e = EqFold{true, ab[0].x * 0x1p-32, fma(ab[0].x, (double)nd, start)};
+    }
+    return e;
+}
+
 // The values of one point group (G points) of a registry integrand: the
 // Philox block (FP64) or pair of blocks (FP32) of every dimension (round 1's
 // product A * c0 given as P, the 64-bit product for the group's first block),
@@ -437,11 +461,32 @@ __device__ __forceinline__ void group_values(
     const PhiloxKeys& keys, const StreamConst& sc, const Coef& coef,
     const typename ModeTraits<MODE>::R* s_pb,
     const typename ModeTraits<MODE>::R* s_c, typename ModeTraits<MODE>::R start, uint64_t P,
-    int nd, typename ModeTraits<MODE>::R (&f)[kGroup<MODE>]) {
+    int nd, typename ModeTraits<MODE>::R (&f)[kGroup<MODE>], const EqFold& eq = EqFold{}) {
     using R = typename ModeTraits<MODE>::R;
     using R2 = typename ModeTraits<MODE>::R2;
     using F = Fn<FN, R>;
     constexpr int G = kGroup<MODE>;
+    if constexpr (MODE == ZMC_FP64 && FN == kSinSum) {
+        if (eq.on) {
+            unsigned long long S[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll 8
+            for (int i = 0; i < nd; ++i) {
+                const uint4 w = philox_from_product(keys, sc, (uint32_t)(P >> 32), (uint32_t)P);
+                P += kPhiloxMulA;
+                S[0] += w.x;
+                S[1] += w.y;
+                S[2] += w.z;
+                S[3] += w.w;
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const double s = __longlong_as_double(0x4330000000000000LL | (long long)S[p]) -
+                                 0x1p52;
+                f[p] = F::finish(fma(eq.al32, s, eq.c0), s_c, nd);
+            }
+            return;
+        }
+    }
     R a[G];
 #pragma unroll
     for (int p = 0; p < G; ++p) a[p] = start;
@@ -497,18 +542,21 @@ __device__ __forceinline__ void sample_unit_fold(
     uint32_t g = g0 + (threadIdx.x & 31);
     uint64_t Pg = (uint64_t)kPhiloxMulA * (uint64_t)(g * B * nd);
     constexpr int G = kGroup<MODE>;
+    const EqFold eq = eq_fold<MODE, FN>(w_coef, nd, start);
     const uint32_t full_end = g1 <= last_group ? g1 : last_group;
     while (g < full_end) {
         for (int j = 0; j < kFlushGroups && g < full_end; ++j, g += 32, Pg += step) {
             R f[G];
-            group_values<MODE, FN, DIM>(keys, sc, WarpCoef<R, R2>{w_coef}, s_pb, s_c, start, Pg, nd, f);
+            group_values<MODE, FN, DIM>(keys, sc, WarpCoef<R, R2>{w_coef}, s_pb, s_c, start, Pg,
+                                        nd, f, eq);
             acc.add(f);
         }
         acc.flush();
     }
     if (g == last_group && g < g1) {
         R f[G];
-        group_values<MODE, FN, DIM>(keys, sc, WarpCoef<R, R2>{w_coef}, s_pb, s_c, start, Pg, nd, f);
+        group_values<MODE, FN, DIM>(keys, sc, WarpCoef<R, R2>{w_coef}, s_pb, s_c, start, Pg, nd,
+                                    f, eq);
         mask_tail(true, tail, f, log_domain<MODE, FN>() ? R(neg_inf()) : R(0));
         acc.add(f);
         acc.flush();
@@ -550,6 +598,7 @@ __device__ __forceinline__ void lane_tile_unit(
     if (!active) return;
     const R start = (R)a0;
     const LaneCoef<R, R2> coef{w_coef, lane_beta + lane};
+    const EqFold eq = eq_fold<MODE, FN>(w_coef, DIM, start);
     const StreamConst sc = stream_const(keys, t, (uint32_t)q, (uint32_t)level);
     SumsFor<MODE, FN> acc(slot, value_scale<MODE, FN>(D));
     const uint64_t step = (uint64_t)kPhiloxMulA * (uint64_t)(DIM * kBlocks<MODE>);
@@ -559,13 +608,13 @@ __device__ __forceinline__ void lane_tile_unit(
     while (g < last) {
         for (int j = 0; j < kFlushGroups && g < last; ++j, ++g, Pg += step) {
             R f[G];
-            group_values<MODE, FN, DIM>(keys, sc, coef, s_pb, s_c, start, Pg, DIM, f);
+            group_values<MODE, FN, DIM>(keys, sc, coef, s_pb, s_c, start, Pg, DIM, f, eq);
             acc.add(f);
         }
         acc.flush();
     }
     R f[G];
-    group_values<MODE, FN, DIM>(keys, sc, coef, s_pb, s_c, start, Pg, DIM, f);
+    group_values<MODE, FN, DIM>(keys, sc, coef, s_pb, s_c, start, Pg, DIM, f, eq);
     mask_tail(true, plan.tail, f, log_domain<MODE, FN>() ? R(neg_inf()) : R(0));
     acc.add(f);
     acc.flush();

@@ -102,6 +102,13 @@ FP64_CASES = [
     W("sel_12167", "genz_gauss", 3, 0.0, 1.0, 23, 24, 4, 1, 1.5, 23,
       [6.0, 3.0, 5.0, 0.4, 0.7, 0.5]),
     W("sel_270400", "genz_corner", 2, 0.0, 1.0, 520, 8, 2, 1, 1.0, 24, [3.0, 5.0]),
+    # The FP64 sine of a sum takes an integer sum of the Philox words when
+    # every dimension has the same width (a cube): a box of unequal widths
+    # keeps the per-dimension FMAs, a 9-D cube runs the integer path past the
+    # 8-way unrolled dimension loop.
+    Workload("sin3_box", "sin_sum", 3, [0.0, -1.0, 2.0], [10.0, 4.0, 3.0], 4, 257, 4, 2, 1.0,
+             31),
+    W("sin9_cube", "sin_sum", 9, 0.0, 2.0, 2, 64, 4, 2, 1.5, 32),
 ]
 
 
