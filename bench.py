@@ -248,8 +248,8 @@ def algorithmic_bytes_per_launch(cells_per_level, n, trials, fp64):
 # kernel's sources it was taken on (profiles/zmc_eval_reduce_sin6d_traffic.md).
 TRAFFIC_CAPTURE = {
     "workload": "sin6d", "fp64": False,
-    "bytes_per_launch": (430592 + 0 + 11683328 + 184357376) / 2,
-    "sources_sha256": "4dcd4bb21b36d2aedb6ef6c1d363548912d4d96195e5b44cbd8e3eb1cc3fb0cd",
+    "bytes_per_launch": (420608 + 0 + 11427072 + 182042624) / 2,
+    "sources_sha256": "5df126020831591c2a38cc67cd66e4362e279a1edc22ea16d0f0f70cf059c70b",
 }
 KERNEL_SOURCES = ["eval_kernel.cuh", "zmc_device.cuh", "zmc_layout.h"]
 
