@@ -1,9 +1,11 @@
 // Kernels (b) and (c): per-cell statistics and the level threshold, cell
 // selection with an ordered block-scan compaction into the next level's work
 // list, and the compensated final reduction.  All run on a fixed grid
-// (kSelGrid CTAs), each CTA owning one contiguous chunk of the level's cells,
-// so results are bit-reproducible on any GPU.  Grid-wide steps (threshold,
-// scan of the per-CTA counts) are done by the last CTA to arrive at a ticket
+// (kSelGrid CTAs) of which a level uses as many as its size needs
+// (active_ctas), each owning one contiguous chunk of the level's cells; the
+// count depends on the level's size only, so results are bit-reproducible on
+// any GPU.  Grid-wide steps (threshold, scan of the per-CTA counts, the
+// level's accepted sums) are done by the last CTA to arrive at a ticket
 // counter; no CTA ever waits on another.
 #include <float.h>
 #include <math.h>
