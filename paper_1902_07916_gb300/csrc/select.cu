@@ -143,6 +143,13 @@ __device__ __forceinline__ double div_rn(double a, double b, double rb) {
     return fma(fma(-q0, b, a), rb, q0);
 }
 
+// Finite test on the exponent bits (integer ALU; the statistics kernel is
+// bound by its FP64 pipe).
+__device__ __forceinline__ bool finite_bits(double x) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7FF0000000000000ULL) !=
+           0x7FF0000000000000ULL;
+}
+
 // Mean and sum of squared deviations of one cell's trial estimates
 // I_t = V S1_t / n, S1_t = row[t * chunks].x.  With TMAX > 0 (and T <= TMAX)
 // the estimates stay in registers between the two passes; with TMAX = 0
@@ -162,7 +169,7 @@ __device__ __forceinline__ void cell_moments(const double2* row, int64_t chunks,
         for (int t = 0; t < TMAX; ++t) {
             if (t < T) {
                 const double S1 = row[t * chunks].x;
-                finite = finite && isfinite(S1);
+                finite = finite && finite_bits(S1);
                 x[t] = div_rn(V * S1, n, rn);
                 s += x[t];
             }
@@ -178,7 +185,7 @@ __device__ __forceinline__ void cell_moments(const double2* row, int64_t chunks,
     } else {
         for (int t = 0; t < T; ++t) {
             const double S1 = row[t * chunks].x;
-            finite = finite && isfinite(S1);
+            finite = finite && finite_bits(S1);
             s += div_rn(V * S1, n, rn);
         }
         mean = div_rn(s, Td, rT);
@@ -280,7 +287,8 @@ __device__ __forceinline__ void cell_stats_body(const Desc* __restrict__ desc, S
     chunk_of(C, G, begin, end);
 
     bool finite = true;
-    double tsum = 0.0, tcount = 0.0;
+    double tsum = 0.0;
+    int tcount = 0;
     for (int64_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
         if (!in_bounds(st, (q + 1) * T * chunks - 1, cap_partial_sums(D), kSiteSumsRead) ||
             !in_bounds(st, q, D.cap_cells, kSiteStatsWrite))
@@ -306,12 +314,12 @@ __device__ __forceinline__ void cell_stats_body(const Desc* __restrict__ desc, S
         const double spread = sqrt(ss * inv_T1);
         cell_stats[q] = make_double2(mean, spread);
         tsum += spread;
-        tcount += 1.0;
+        ++tcount;
     }
     if (!finite) atomicMax(&st->status, ZMC_ERR_NONFINITE);
     // this CTA's count, mean and M2 of its spreads (the second pass reads
     // back what this thread wrote)
-    const double2 sc = block_sum2(tsum, tcount);
+    const double2 sc = block_sum2(tsum, (double)tcount);
     const double cmean = sc.y > 0.0 ? sc.x / sc.y : 0.0;
     double m2 = 0.0;
     for (int64_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
