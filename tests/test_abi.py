@@ -146,3 +146,21 @@ def test_work_plan_and_tuning_validation_on_host(zmc):
         zmc.zmc_set_tuning(h, 0)
     finally:
         zmc.zmc_destroy(h)
+
+
+def test_build_id_follows_the_sources(tmp_path, monkeypatch):
+    # The tuner's file cache (ZMC_TUNE_CACHE) keys its entries by this id:
+    # the same sources give the same id, the checked build and any changed
+    # source another.
+    import shutil
+    from paper_1902_07916_gb300 import build as b
+    srcs = [os.path.join(b.CSRC, f) for f in b.SOURCES]
+    a = b._build_id(srcs, False)
+    assert re.fullmatch(r"0x[0-9a-f]{16}ULL", a)
+    assert a == b._build_id(srcs, False)
+    assert a != b._build_id(srcs, True)
+    csrc = tmp_path / "csrc"
+    shutil.copytree(b.CSRC, csrc)
+    (csrc / "select.cu").write_text((csrc / "select.cu").read_text() + "\n")
+    monkeypatch.setattr(b, "CSRC", str(csrc))
+    assert b._build_id([str(csrc / f) for f in b.SOURCES], False) != a
